@@ -1,0 +1,217 @@
+"""CPU oracle for massively parallel local Monte Carlo of hard disks.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, sequential, obviously
+correct statement of what the GPU library computes:
+
+* ``hd_oracle.c`` - the checkerboard MPMC chain of Engel et al.,
+  arXiv:1211.1645, Sec. II.B (four colours, random colour order, random grid
+  shift after each sweep, shuffled serial trials inside a cell, moves that
+  leave the cell rejected), in plain FP64 and in cell-relative fixed point;
+  the contact-shell pair histogram (numerator of Eq. 2) and the local /
+  global bond order psi_6 (Eq. 8).
+* this module - ctypes access to it, plus the g(r) normalisation (Eq. 2),
+  the quartic contact extrapolation (Sec. II.C.1) and the contact-value
+  pressure (Eq. 4) in numpy.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA library.
+
+Pins (tests/test_oracle_*.py): Philox known-answer vectors; never-overlap
+invariant; exact two-disk separation law and two-disk pressure; hard-disk
+virial series at low density; ideal-gas g(r) = (N-1)/N; exact synthetic
+quartic recovery; frame-change invariance; psi_6 of hand-built hexagonal
+shells and its rotation / reflection covariance; brute-force neighbour and
+pair enumeration.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hd_oracle.c")
+_SO = os.path.join(_HERE, "_build", "libhd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FP64 = 0
+FIXED = 1
+FORMS = {"fp64": FP64, "fixed": FIXED}
+LATTICES = {"square": 0, "triangular": 1}
+
+# 2^24 fixed-point units per sigma
+FX_SCALE = 16777216.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, IEEE order kept)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm",
+        ])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        c = ctypes
+        P = c.c_void_p
+        lib.hdo_create.restype = P
+        lib.hdo_create.argtypes = [c.c_int64, c.c_double, c.c_double, c.c_uint64, c.c_int,
+                                   c.c_int, c.c_int, c.c_double, c.POINTER(c.c_int)]
+        lib.hdo_destroy.argtypes = [P]
+        lib.hdo_sweep.argtypes = [P, c.c_int64]
+        lib.hdo_positions.argtypes = [P, P]
+        lib.hdo_set_positions.argtypes = [P, P]
+        lib.hdo_set_positions.restype = c.c_int
+        lib.hdo_stats.argtypes = [P, P, P]
+        lib.hdo_geometry.argtypes = [P, P]
+        lib.hdo_frame.argtypes = [P, P, P, P]
+        lib.hdo_histogram.argtypes = [P, c.c_int, c.c_double, c.c_int, P]
+        lib.hdo_histogram.restype = c.c_int
+        lib.hdo_psi6.argtypes = [P, c.c_int, P, P]
+        lib.hdo_psi6.restype = c.c_int
+        lib.hdo_philox4x32_10.argtypes = [P, P, P]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: four 32-bit counter words, two key words."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.hdo_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+class OracleChain:
+    """One MPMC chain: N disks of radius sigma = 1 at packing fraction eta.
+
+    form      "fp64" or "fixed" (cell-relative 2^-24 sigma integers)
+    lattice   "square" or "triangular" (odd rows offset by half a spacing)
+    nt        trial moves per occupied active cell per pass (0: ceil(N/m^2))
+    cell_min  minimum cell side (>= 2 sigma)
+    """
+
+    def __init__(self, N: int, eta: float, delta: float, seed: int, form: str = "fp64",
+                 lattice: str = "square", nt: int = 0, cell_min: float = 2.0):
+        lib = _load()
+        st = ctypes.c_int(0)
+        self._h = lib.hdo_create(int(N), float(eta), float(delta), int(seed), FORMS[form],
+                                 LATTICES[lattice], int(nt), float(cell_min), ctypes.byref(st))
+        if not self._h:
+            raise ValueError(f"oracle rejected N={N} eta={eta} delta={delta} form={form} (status {st.value})")
+        self.N = int(N)
+        self.form = form
+        self.eta_requested = float(eta)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().hdo_destroy(h)
+            self._h = None
+
+    def sweep(self, n: int = 1) -> None:
+        _load().hdo_sweep(self._h, int(n))
+
+    def positions(self) -> np.ndarray:
+        out = np.empty((self.N, 2), dtype=np.float64)
+        _load().hdo_positions(self._h, _ptr(out))
+        return out
+
+    def set_positions(self, xy) -> None:
+        a = np.ascontiguousarray(xy, dtype=np.float64).reshape(self.N, 2)
+        _load().hdo_set_positions(self._h, _ptr(a))
+
+    def stats(self):
+        a = np.zeros(1, np.uint64)
+        b = np.zeros(1, np.uint64)
+        _load().hdo_stats(self._h, _ptr(a), _ptr(b))
+        return int(a[0]), int(b[0])
+
+    def geometry(self) -> dict:
+        g = np.zeros(10, np.float64)
+        _load().hdo_geometry(self._h, _ptr(g))
+        L = g[0]
+        return {"L": L, "w": g[1], "delta": g[2], "m": int(g[3]), "W": int(g[4]), "LF": int(g[5]),
+                "D": int(g[6]), "nt": int(g[7]), "max_occupancy": int(g[8]), "sweeps": int(g[9]),
+                "eta": self.N * np.pi / (L * L)}
+
+    def frame(self):
+        cells = np.empty((self.N, 2), np.int32)
+        offs = np.empty((self.N, 2), np.float64)
+        shift = np.empty(2, np.float64)
+        _load().hdo_frame(self._h, _ptr(cells), _ptr(offs), _ptr(shift))
+        return cells, offs, shift
+
+    def histogram(self, K: int, dr: float, brute: bool = False) -> np.ndarray:
+        out = np.zeros(int(K), np.uint64)
+        rc = _load().hdo_histogram(self._h, int(K), float(dr), int(bool(brute)), _ptr(out))
+        if rc != 0:
+            raise ValueError(f"histogram reach exceeds the box (status {rc})")
+        return out
+
+    def psi6(self, brute: bool = False):
+        loc = np.empty((self.N, 2), np.float64)
+        glob = np.empty(2, np.float64)
+        rc = _load().hdo_psi6(self._h, int(bool(brute)), _ptr(loc), _ptr(glob))
+        if rc != 0:
+            raise ValueError(f"psi6 neighbour search failed (status {rc})")
+        return loc[:, 0] + 1j * loc[:, 1], complex(glob[0], glob[1])
+
+    def realised_dr(self, dr: float) -> float:
+        """Bin width actually used: dr itself (FP64) or dr on the 2^-24 grid."""
+        if self.form == "fixed":
+            return float(np.round(dr * FX_SCALE)) / FX_SCALE
+        return float(dr)
+
+
+def g_of_r(counts, N: int, L: float, dr: float):
+    """Eq. 2: g(r_k) = (n_k / p) / (2 pi r_k dr / V) at bin centres r_k.
+
+    p = N^2 / 2, the reading under which Eq. 4 is exact at finite N (for two
+    disks it reproduces beta P = 1/V + 1/(V - 4 pi sigma^2) exactly)."""
+    n = np.asarray(counts, dtype=np.float64)
+    K = n.shape[-1]
+    r = 2.0 + (np.arange(K, dtype=np.float64) + 0.5) * dr
+    V = L * L
+    p = 0.5 * float(N) * float(N)
+    return r, (n / p) / (2.0 * np.pi * r * dr / V)
+
+
+def contact_fit(r, g, degree: int = 4) -> float:
+    """Sec. II.C.1: least-squares polynomial of the given degree (fourth
+    order in the paper) in x = r - 2 sigma, extrapolated to x = 0."""
+    x = np.asarray(r, dtype=np.float64) - 2.0
+    A = np.vander(x, degree + 1, increasing=True)
+    coef, *_ = np.linalg.lstsq(A, np.asarray(g, dtype=np.float64), rcond=None)
+    return float(coef[0])
+
+
+def contact_pressure(counts, N: int, L: float, dr: float, degree: int = 4) -> dict:
+    """Eq. 4: beta P / rho = 1 + 2 eta g(2 sigma+), with eta = N pi / L^2.
+    P* = beta P (2 sigma)^2 (Eq. 1)."""
+    r, g = g_of_r(counts, N, L, dr)
+    g0 = contact_fit(r, g, degree)
+    eta = N * np.pi / (L * L)
+    bp_rho = 1.0 + 2.0 * eta * g0
+    return {"g0": g0, "betaP_over_rho": bp_rho, "Pstar": bp_rho * 4.0 * N / (L * L), "eta": eta,
+            "g": g, "r": r}
