@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: hard-disk trial moves per second at N = 1024^2, eta = 0.716.
+
+One step = S checkerboard sweeps (each: cell rebuild on a freshly shifted
+grid + four colour passes) followed by one measurement (contact-histogram
+pressure and global psi_6), i.e. one pass of the whole hot path.  The
+headline form is the cell-relative fixed-point chain; the plain FP64 chain
+runs the same seed schedule and is reported beside it.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the library's stream; L2 is flushed (a 256 MB write) before every timed
+step, outside the events.  Under torchrun each rank runs its own replica
+(seed + rank, weak scaling) and rank 0 reports the max time over ranks.
+
+--impl reference times the CPU oracle (one core) on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "disk trial moves/s at N=1M, η=0.716: fixed-point batched vs plain FP64"
+UNIT = "trial moves/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--sweeps-per-step", type=int, default=100)
+    p.add_argument("--N", type=int, default=1024 * 1024)
+    p.add_argument("--eta", type=float, default=0.716)
+    p.add_argument("--delta", type=float, default=0.1)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--form", choices=["fixed", "fp64"], default="fixed")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU oracle sample budget")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU, independent replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max_sum(world, tmax: float, tsum: float, device):
+    """Max of tmax and sum of tsum over ranks."""
+    if world == 1:
+        return tmax, tsum
+    import torch
+    import torch.distributed as dist
+    a = torch.tensor([tmax], dtype=torch.float64, device=device)
+    b = torch.tensor([tsum], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def time_form(args, form, rank, world, steps, warmup, sampler=None):
+    """Device-resident timing of `steps` steps of one form; returns a dict."""
+    import torch
+
+    import paper_1211_1645_gb300 as hd
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form)
+    sysg.set_stream(stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    S = args.sweeps_per_step
+
+    def step():
+        sysg.sweep(S)
+        sysg.pressure(want_hist=False)
+        sysg.psi6(want_local=False)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    att0 = int(sysg.stats()[0][0])
+    l0 = sysg.kernel_times()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    attempts = int(sysg.stats()[0][0]) - att0
+    l1 = sysg.kernel_times()
+    launches = sum(l1[k][1] - l0[k][1] for k in l1)
+
+    # instrumented pass: per-kernel device time on the same workload
+    sysg.profile(True)
+    for _ in range(2):
+        flush.zero_()
+        step()
+    kt = sysg.kernel_times()
+    sysg.profile(False)
+    geo = sysg.geometry()
+    sysg.close()
+    return {"ms": ms, "attempts": attempts, "launches": launches, "clocks": clocks, "kernel_times": kt,
+            "geometry": geo}
+
+
+def time_e2e(args, form, rank, steps):
+    """Same metric through the public API with host buffers: each step uploads
+    the configuration, sweeps, measures and reads the configuration back."""
+    import numpy as np
+    import torch
+
+    import paper_1211_1645_gb300 as hd
+
+    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form)
+    xy = np.ascontiguousarray(sysg.positions())
+    S = args.sweeps_per_step
+    att0 = int(sysg.stats()[0][0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sysg.set_positions(xy)
+        sysg.sweep(S)
+        sysg.pressure(want_hist=False)
+        sysg.psi6(want_local=False)
+        xy = sysg.positions()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    attempts = int(sysg.stats()[0][0]) - att0
+    sysg.close()
+    return {"value": attempts / dt, "unit": UNIT, "h2d_bytes_per_step": int(xy.nbytes),
+            "d2h_bytes_per_step": int(xy.nbytes) + 16 + 16}
+
+
+def algorithmic_pass_bytes(N, m, form):
+    """Minimum DRAM traffic of one colour pass: every cell's
+    occupancy byte and every disk's coordinates read once, the active quarter
+    of the coordinates written back."""
+    coord = 8 if form == "fixed" else 16
+    return m * m + N * coord + (N // 4) * coord
+
+
+def cpu_oracle(args, form, budget_s):
+    import oracle
+    oracle.build()
+    o = oracle.OracleChain(args.N, args.eta, args.delta, args.seed, form=form)
+    a0, _ = o.stats()
+    t0 = time.perf_counter()
+    sweeps = 0
+    while sweeps < 2 or time.perf_counter() - t0 < budget_s:
+        o.sweep(1)
+        sweeps += 1
+    dt = time.perf_counter() - t0
+    a1, _ = o.stats()
+    return {"value": (a1 - a0) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} sweeps of the {form} oracle chain at N={args.N}, eta={args.eta}, seed {args.seed} "
+                      f"(single thread, {dt:.1f} s)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU; use --impl reference for the CPU oracle")
+    import paper_1211_1645_gb300 as hd
+    hd.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    main = time_form(args, args.form, rank, world, args.steps, args.warmup, sampler)
+    tmax, att_sum = reduce_max_sum(world, main["ms"], float(main["attempts"]), dev)
+    value = att_sum / (tmax / 1e3)
+    fp64 = None
+    if not args.no_fp64 and args.form != "fp64":
+        r = time_form(args, "fp64", rank, world, max(1, args.steps // 2), 1)
+        t64, a64 = reduce_max_sum(world, r["ms"], float(r["attempts"]), dev)
+        fp64 = {"value": a64 / (t64 / 1e3), "ms_per_step": t64 / max(1, args.steps // 2),
+                "pass_ms_avg": r["kernel_times"]["pass"][0] / max(1, r["kernel_times"]["pass"][1])}
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2))
+    if rank != 0:
+        return
+    kt = main["kernel_times"]
+    geo = main["geometry"]
+    pass_ms, pass_n = kt["pass"]
+    pass_avg_s = pass_ms / max(1, pass_n) / 1e3
+    peak, peak_kind = peaks()
+    alg = algorithmic_pass_bytes(args.N, geo["m"], args.form)
+    achieved = alg / pass_avg_s / 1e9 if pass_avg_s > 0 else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32" if args.form == "fixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"MPMC hard disks N={args.N} eta={args.eta} delta={args.delta}, "
+                               f"{args.form} form, {args.sweeps_per_step} sweeps + 1 pressure/psi6 measurement per step",
+                   "N": args.N, "eta": args.eta, "sweeps_per_step": args.sweeps_per_step, "cells_per_side": geo["m"],
+                   "trials_per_cell": geo["trials_per_cell"], "l2": "flushed before each timed step (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_pass (one colour pass)", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_us": pass_avg_s * 1e6},
+        "gpu_launches": main["launches"],
+        "clocks": main["clocks"],
+        "kernel_ms_per_step": {k: v[0] / 2 for k, v in kt.items() if v[1]},
+        "fp64": fp64,
+        "e2e": e2e,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle(args, args.form, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    per = []
+    total_budget = max(2.0, 30.0 / max(1, args.steps + args.warmup))
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle(args, args.form, total_budget)
+        if k >= args.warmup:
+            per.append(r)
+    value = statistics.mean(r["value"] for r in per)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (time.perf_counter() - t0) * 1e3 / max(1, args.steps + args.warmup),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32" if args.form == "fixed" else "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"MPMC hard disks N={args.N} eta={args.eta} delta={args.delta}, {args.form} form "
+                               f"(CPU oracle, bounded sample per step)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": per[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * hd.h -- C ABI of the GB300 library for massively parallel local Monte Carlo
+ * (MPMC) of hard disks: Engel, Anderson, Glotzer, Isobe, Bernard, Krauth,
+ * "Hard-disk equation of state", arXiv:1211.1645.
+ *
+ * The library owns all device state.  Callers pass plain host pointers and
+ * sizes; no call takes or returns a framework type.  Every call returns an
+ * hd_status and never aborts the process.  Output-returning calls synchronise
+ * the context's stream.  A CUDA failure or a device-side error flag leaves the
+ * context in a sticky error state: every later call except hd_destroy returns
+ * HD_ERR_STATE.
+ *
+ * Units: sigma is the disk radius.  Positions are in [0, L) x [0, L) with
+ * periodic boundaries; L = sqrt(N pi sigma^2 / eta) (Sec. II.A).
+ *
+ * A context holds R >= 1 independent chains ("replicas").  hd_init makes
+ * R = 1; hd_batch_init makes R chains of different N and eta that advance
+ * together in the same kernel launches.  Arrays documented as [R] or
+ * [sum N_r] hold one entry per replica / per disk of every replica,
+ * replica-major, disks in id order.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hd_ctx hd_ctx;
+
+typedef enum hd_status {
+    HD_OK = 0,
+    HD_ERR_ARG = 1,      /* invalid argument; the context is unchanged           */
+    HD_ERR_CUDA = 2,     /* a CUDA runtime call failed; the context is poisoned  */
+    HD_ERR_OVERFLOW = 3, /* a cell held more disks than its capacity (device)   */
+    HD_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                  */
+    HD_ERR_REACH = 5,    /* a measurement stencil would wrap around the box      */
+    HD_ERR_STATE = 6     /* the context is in a sticky error state               */
+} hd_status;
+
+typedef enum hd_precision {
+    HD_FP64 = 0,   /* plain IEEE double, no FMA contraction                     */
+    HD_FIXED32 = 1 /* cell-relative int32 in units of 2^-24 sigma, int64 test  */
+} hd_precision;
+
+typedef enum hd_lattice {
+    HD_LATTICE_SQUARE = 0,    /* n = ceil(sqrt N) columns of spacing L/n          */
+    HD_LATTICE_TRIANGULAR = 1 /* same, odd rows shifted by half a spacing        */
+} hd_lattice;
+
+/* Options shared by all replicas of a context.  Zero / negative fields take
+ * the default given in brackets. */
+typedef struct hd_opts {
+    int32_t precision;       /* hd_precision [HD_FP64]                              */
+    int32_t lattice;         /* hd_lattice [HD_LATTICE_SQUARE]                      */
+    int32_t trials_per_cell; /* n_t, trial moves per occupied active cell and pass;
+                                Sec. II.B fixes it independent of occupancy
+                                [ceil(N / m^2), per replica]                        */
+    int32_t hist_bins;       /* K, contact-histogram bins [50]                      */
+    double hist_dr;          /* bin width in sigma [1e-3]; Sec. II.C.1              */
+    double cell_min;         /* minimum cell side in sigma, >= 2 [2]; Sec. II.B     */
+    int32_t block_threads;   /* threads per block of the sweep kernels [128]        */
+    int32_t reserved;
+} hd_opts;
+
+/* Geometry of one replica as realised by the library. */
+typedef struct hd_geometry {
+    int64_t N;
+    int32_t m;          /* cells per side (even, >= 4)                            */
+    int32_t capacity;   /* disk slots per cell                                    */
+    int32_t trials_per_cell;
+    int32_t precision;
+    int32_t hist_bins;  /* K of the contact histogram                             */
+    int32_t reserved;
+    double L;           /* box side in sigma (fixed form: m * W * 2^-24)          */
+    double w;           /* cell side in sigma                                     */
+    double delta;       /* maximum displacement per axis in sigma (realised)      */
+    double eta;         /* realised packing fraction N pi / L^2                   */
+    double hist_dr;     /* realised histogram bin width in sigma                  */
+    int64_t sweeps;     /* sweeps done                                            */
+} hd_geometry;
+
+/* Fill *o with the defaults. */
+void hd_default_opts(hd_opts *o);
+
+/* Human-readable name of a status code (static storage). */
+const char *hd_status_string(hd_status s);
+
+/*
+ * Create one chain of N disks of radius sigma at packing fraction eta
+ * (Sec. II.A), trial displacements uniform in [-delta, delta]^2 (sigma units
+ * scale with sigma), Philox4x32-10 keyed by seed.  Disks start on the lattice
+ * of opts->lattice, binned into an unshifted grid of m x m cells where m is
+ * the largest even integer with L/m >= cell_min (Sec. II.B).
+ * Errors: HD_ERR_ARG if N < 2, eta <= 0, the lattice would overlap
+ * (L / ceil(sqrt N) < 2 sigma), m < 4, delta < 0 or delta >= cell side, a
+ * cell could hold more than 9 disks, or the fixed form would overflow int32.
+ * *out receives the context (NULL on error); release it with hd_destroy.
+ */
+hd_status hd_init(hd_ctx **out, int64_t N, double eta, double sigma, double delta,
+                  uint64_t seed, const hd_opts *opts);
+
+/*
+ * Create R independent chains in one context (the equation-of-state scan of
+ * Sec. IV.A as one batch).  N[R], eta[R], delta[R], seed[R] are per replica;
+ * sigma and opts are shared.  Same errors as hd_init, per replica.
+ */
+hd_status hd_batch_init(hd_ctx **out, int32_t R, const int64_t *N, const double *eta, double sigma,
+                        const double *delta, const uint64_t *seed, const hd_opts *opts);
+
+/* Release all device and host memory of the context.  NULL is allowed. */
+hd_status hd_destroy(hd_ctx *ctx);
+
+/* Launch all later work of the context on this CUDA stream (a cudaStream_t
+ * passed as void*; NULL = the legacy default stream). */
+hd_status hd_set_stream(hd_ctx *ctx, void *stream);
+
+/*
+ * Advance every replica by n checkerboard sweeps (Sec. II.B).  One sweep:
+ * draw a uniform grid shift in [0, w)^2 and a random order of the four
+ * colours; move every disk into the shifted cell frame (cell lists rebuilt,
+ * occupants ordered by id); then, for each colour in that order, every
+ * active cell shuffles its occupants and makes n_t serial trial moves,
+ * rejecting moves that leave the cell or overlap a disk of the 3 x 3 cell
+ * neighbourhood.  Asynchronous on the context stream.  n >= 0.
+ */
+hd_status hd_sweep(hd_ctx *ctx, int64_t n);
+
+/*
+ * Contact-value pressure (Eqs. 2 and 4): histogram of pair distances in
+ * [2 sigma, 2 sigma + K dr) with K bins, g(r_k) = (n_k / p) / (2 pi r_k dr /
+ * V) at bin centres with p = N^2 / 2, least-squares quartic in r - 2 sigma
+ * extrapolated to contact (Sec. II.C.1), beta P / rho = 1 + 2 eta g(2 sigma+).
+ * Outputs (host, caller-owned, any may be NULL): betaP_over_rho[R],
+ * g_contact[R], hist[R * K] raw counts.  Synchronises.
+ * Errors: HD_ERR_REACH if 2 sigma + K dr needs a cell stencil wider than the
+ * box.
+ */
+hd_status hd_pressure(hd_ctx *ctx, double *betaP_over_rho, double *g_contact, uint64_t *hist);
+
+/*
+ * Bond-orientational order (Eq. 8): psi_j = (1/6) sum over the six nearest
+ * neighbours (minimum image, ties by lower id) of exp(6 i phi_jk), phi from
+ * the +x axis; Psi_6 = (1/N) sum_j psi_j per replica.  Outputs (host,
+ * caller-owned, any may be NULL): re[R], im[R], local[2 * sum N_r]
+ * interleaved (re, im) by disk id.  The fixed form computes psi_j in float
+ * and reduces in double.  Synchronises.
+ * Errors: HD_ERR_REACH if a disk has fewer than six neighbours within the
+ * largest stencil the box allows.
+ */
+hd_status hd_psi6(hd_ctx *ctx, double *re, double *im, double *local);
+
+/* Global positions (host, caller-owned, [2 * sum N_r] interleaved x, y in
+ * [0, L), by disk id).  Synchronises. */
+hd_status hd_positions(hd_ctx *ctx, double *xy);
+
+/* Same, into a device buffer of 2 * sum N_r doubles.  Asynchronous. */
+hd_status hd_positions_device(hd_ctx *ctx, double *xy_device);
+
+/*
+ * Replace all positions (host, [2 * sum N_r], periodic images allowed).  The
+ * cell frame is reset to shift zero; counters and the sweep index are kept.
+ * Overlapping input is accepted (measurements then count it); the fixed form
+ * rounds to the 2^-24 sigma grid.  Synchronises.
+ * Errors: HD_ERR_OVERFLOW if a cell would hold more disks than its capacity.
+ */
+hd_status hd_set_positions(hd_ctx *ctx, const double *xy);
+
+/* Attempted and accepted trial moves since creation, per replica [R].
+ * Attempts count every trial, including moves rejected at the cell
+ * boundary.  Synchronises. */
+hd_status hd_stats(hd_ctx *ctx, uint64_t *attempts, uint64_t *accepts);
+
+/* Geometry of replica r. */
+hd_status hd_get_geometry(hd_ctx *ctx, int32_t r, hd_geometry *g);
+
+/* Number of replicas of the context. */
+int32_t hd_replicas(const hd_ctx *ctx);
+
+/*
+ * Instrumentation (no counterpart in the paper).  The library counts every
+ * kernel it launches, by class.  With profiling enabled it also brackets each
+ * launch with CUDA events on the context stream; hd_kernel_times then
+ * synchronises and reports the summed device time per class.  Enabling
+ * (enable != 0) resets both tallies; disabling keeps them readable.
+ * ms[HD_KERNEL_CLASSES] and launches[HD_KERNEL_CLASSES] are host arrays, either
+ * may be NULL.
+ */
+typedef enum hd_kernel_class {
+    HD_K_DRAWS = 0,      /* per-sweep shift and colour-order draws           */
+    HD_K_REBUILD = 1,    /* move disks into the shifted frame, rebuild cells  */
+    HD_K_PASS = 2,       /* one colour pass of trial moves                    */
+    HD_K_HIST = 3,       /* contact-shell pair histogram                      */
+    HD_K_FIT = 4,        /* g(r) normalisation, quartic fit, pressure         */
+    HD_K_PSI6 = 5,       /* local psi_6                                       */
+    HD_K_PSI6_REDUCE = 6,/* global Psi_6 reduction                            */
+    HD_K_POSITIONS = 7,  /* cell frame to global positions                    */
+    HD_KERNEL_CLASSES = 8
+} hd_kernel_class;
+
+hd_status hd_profile(hd_ctx *ctx, int32_t enable);
+hd_status hd_kernel_times(hd_ctx *ctx, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HD_H */

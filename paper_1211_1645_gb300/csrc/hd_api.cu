@@ -1,0 +1,694 @@
+// hd_api.cu -- the C ABI declared in include/hd.h: context creation
+// (geometry of Sec. II.A/B, initial lattice, cell binning), sweep sequencing,
+// measurements and read-back.  Host code only; all per-disk work runs in the
+// kernels of hd_sweep.cu and hd_measure.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hd.h"
+#include "hd_kernels.h"
+
+using hd::CellBufs;
+using hd::Frame;
+using hd::Rep;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kFx = 16777216.0;  // 2^24 fixed-point units per sigma
+constexpr int kMaxBins = 512;
+
+struct Plan {
+    Rep rep;
+    int cap;
+    int64_t nlat;   // lattice columns
+    double eta_req;
+};
+
+}  // namespace
+
+struct hd_ctx {
+    int R = 0;
+    bool fixed = false;
+    int cap = 4;
+    int K = 50;
+    int lattice = 0;
+    int threads = 128;
+    double sigma = 1.0;
+    std::vector<Rep> reps;
+    std::vector<int64_t> nlat;
+    int64_t Ntot = 0, Ctot = 0;
+    int blocks_cell = 0, blocks_act = 0;
+    Rep* reps_d = nullptr;
+    CellBufs buf[2] = {};
+    int cur = 0;
+    Frame* table = nullptr;
+    Frame* frame = nullptr;
+    uint64_t* sweep_ctr = nullptr;
+    unsigned long long* counters = nullptr;
+    int* err = nullptr;
+    unsigned long long* hist = nullptr;
+    double* edges = nullptr;
+    long long* edgesF = nullptr;
+    double* fit = nullptr;
+    double2* psi_local = nullptr;
+    double2* psi_part = nullptr;
+    double* psi_res = nullptr;
+    double* xy = nullptr;
+    cudaStream_t stream = nullptr;
+    hd_status sticky = HD_OK;
+    std::vector<int64_t> sweeps;
+    std::vector<void*> allocs;
+    // instrumentation: launch tallies always, event timing when enabled
+    int64_t launches[HD_KERNEL_CLASSES] = {};
+    double kernel_ms[HD_KERNEL_CLASSES] = {};
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;    // pool, used in start/stop pairs
+    std::vector<int> ev_class;      // class of each pending pair
+    size_t ev_used = 0;
+
+    hd::LaunchCfg cfg() const {
+        hd::LaunchCfg c;
+        c.reps = reps_d;
+        c.R = R;
+        c.cap = cap;
+        c.fixed = fixed;
+        c.threads = threads;
+        c.blocks_cell = blocks_cell;
+        c.blocks_act = blocks_act;
+        c.stream = stream;
+        return c;
+    }
+};
+
+namespace {
+
+hd_status fail_cuda(hd_ctx* ctx) {
+    ctx->sticky = HD_ERR_CUDA;
+    return HD_ERR_CUDA;
+}
+
+#define HD_CK(ctx, call)                                   \
+    do {                                                   \
+        if ((call) != cudaSuccess) return fail_cuda(ctx);  \
+    } while (0)
+
+template <class T>
+bool dev_alloc(hd_ctx* ctx, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
+    ctx->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+}
+
+// Geometry of one chain (Sec. II.A, II.B).  Lengths in units of sigma.
+hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64_t seed, const hd_opts& o,
+                       Plan& pl) {
+    if (N < 2 || N > (int64_t(1) << 31) - 1 || !(eta > 0.0) || !(sigma > 0.0) || !(delta >= 0.0))
+        return HD_ERR_ARG;
+    const bool fixed = o.precision == HD_FIXED32;
+    const double L = std::sqrt(double(N) * kPi / eta);
+    const int m = 2 * int(std::floor(L / (2.0 * o.cell_min)));
+    if (m < 4) return HD_ERR_ARG;
+    const double w = L / double(m);
+    if (!(w < 8.0)) return HD_ERR_ARG;
+    int64_t n = int64_t(std::ceil(std::sqrt(double(N))));
+    while (n * n < N) ++n;
+    while ((n - 1) * (n - 1) >= N) --n;
+    if (L / double(n) < 2.0) return HD_ERR_ARG;  // the initial lattice would overlap
+    const double dhat = delta / sigma;
+    const int64_t W = std::llround(w * kFx);
+    const int64_t D = std::llround(dhat * kFx);
+    if (fixed) {
+        if (W >= (int64_t(1) << 29) || 2 * D + 1 >= (int64_t(1) << 32) || D >= W) return HD_ERR_ARG;
+    } else if (!(dhat < w)) {
+        return HD_ERR_ARG;
+    }
+    const double wr = fixed ? double(W) / kFx : w;
+    const int kk = int(std::floor(wr / std::sqrt(2.0))) + 1;  // sub-squares of side < sqrt(2) sigma
+    pl.cap = kk * kk;
+    if (pl.cap > 9) return HD_ERR_ARG;
+    Rep& r = pl.rep;
+    std::memset(&r, 0, sizeof(Rep));
+    r.N = N;
+    r.m = m;
+    r.hm = m / 2;
+    const int64_t ncell = int64_t(m) * m;
+    r.nt = o.trials_per_cell > 0 ? o.trials_per_cell : int((N + ncell - 1) / ncell);
+    r.W = int32_t(W);
+    r.D = int32_t(D);
+    r.LF = int64_t(m) * W;
+    r.w = w;
+    r.w_below = std::nextafter(w, 0.0);
+    r.L = L;
+    r.delta = dhat;
+    r.sigma = sigma;
+    r.key0 = uint32_t(seed & 0xffffffffu);
+    r.key1 = uint32_t(seed >> 32);
+    pl.nlat = n;
+    pl.eta_req = eta;
+    return HD_OK;
+}
+
+// FP64 cell binning of a global coordinate t in [0, L).
+void bin_fp64(double t, const Rep& r, int& c, double& u) {
+    int cc = int(t / r.w);
+    if (cc > r.m - 1) cc = r.m - 1;
+    if (cc < 0) cc = 0;
+    double uu = t - double(cc) * r.w;
+    if (uu < 0.0 && cc > 0) {
+        cc -= 1;
+        uu = t - double(cc) * r.w;
+    }
+    if (uu >= r.w && cc < r.m - 1) {
+        cc += 1;
+        uu = t - double(cc) * r.w;
+    }
+    if (uu < 0.0) uu = 0.0;
+    if (uu >= r.w) uu = r.w_below;
+    c = cc;
+    u = uu;
+}
+
+// Host image of one cell-list generation.
+struct HostCells {
+    std::vector<uint8_t> cnt;
+    std::vector<double> pos64;   // 2 per slot
+    std::vector<int32_t> posfx;  // 2 per slot
+    std::vector<int32_t> pid;
+};
+
+// Insert disk `id` of replica r with global coordinates (sigma units, or exact
+// fixed-point integers) into the unshifted cell frame.
+bool bin_disk(const hd_ctx* ctx, const Rep& rep, HostCells& h, int64_t id, double x, double y, int64_t X,
+              int64_t Y) {
+    int cx, cy;
+    double ux = 0.0, uy = 0.0;
+    int32_t fx = 0, fy = 0;
+    if (ctx->fixed) {
+        cx = int(X / rep.W);
+        cy = int(Y / rep.W);
+        fx = int32_t(X % rep.W);
+        fy = int32_t(Y % rep.W);
+    } else {
+        bin_fp64(x, rep, cx, ux);
+        bin_fp64(y, rep, cy, uy);
+    }
+    const int64_t cell = rep.cell_off + int64_t(cy) * rep.m + cx;
+    const int k = h.cnt[cell];
+    if (k >= ctx->cap) return false;
+    const int64_t slot = cell * ctx->cap + k;
+    if (ctx->fixed) {
+        h.posfx[2 * slot] = fx;
+        h.posfx[2 * slot + 1] = fy;
+    } else {
+        h.pos64[2 * slot] = ux;
+        h.pos64[2 * slot + 1] = uy;
+    }
+    h.pid[slot] = int32_t(id);
+    h.cnt[cell] = uint8_t(k + 1);
+    return true;
+}
+
+void host_cells_init(const hd_ctx* ctx, HostCells& h) {
+    h.cnt.assign(size_t(ctx->Ctot), 0);
+    h.pid.assign(size_t(ctx->Ctot) * ctx->cap, 0);
+    if (ctx->fixed) h.posfx.assign(size_t(ctx->Ctot) * ctx->cap * 2, 0);
+    else h.pos64.assign(size_t(ctx->Ctot) * ctx->cap * 2, 0.0);
+}
+
+hd_status upload_cells(hd_ctx* ctx, const HostCells& h) {
+    const size_t slots = size_t(ctx->Ctot) * ctx->cap;
+    CellBufs& b = ctx->buf[ctx->cur];
+    HD_CK(ctx, cudaMemcpyAsync(b.cnt, h.cnt.data(), h.cnt.size(), cudaMemcpyHostToDevice, ctx->stream));
+    HD_CK(ctx, cudaMemcpyAsync(b.pid, h.pid.data(), slots * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->fixed)
+        HD_CK(ctx, cudaMemcpyAsync(b.pos, h.posfx.data(), slots * 2 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    else
+        HD_CK(ctx, cudaMemcpyAsync(b.pos, h.pos64.data(), slots * 2 * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    std::vector<Frame> zero(size_t(ctx->R));
+    std::memset(zero.data(), 0, zero.size() * sizeof(Frame));
+    HD_CK(ctx, cudaMemcpyAsync(ctx->frame, zero.data(), zero.size() * sizeof(Frame), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+// Read the device error flag after a synchronisation.  Overflow is sticky
+// (disks were dropped); a measurement reach failure is reported once.
+hd_status check_flags(hd_ctx* ctx) {
+    int flag = 0;
+    HD_CK(ctx, cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag & 1) {
+        ctx->sticky = HD_ERR_OVERFLOW;
+        return HD_ERR_OVERFLOW;
+    }
+    if (flag & 2) {
+        HD_CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+        HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return HD_ERR_REACH;
+    }
+    return HD_OK;
+}
+
+void free_ctx(hd_ctx* ctx) {
+    if (!ctx) return;
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    delete ctx;
+}
+
+// Fold the pending event pairs into the per-class totals.
+bool prof_flush(hd_ctx* ctx) {
+    if (ctx->ev_used == 0) return true;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return false;
+    for (size_t i = 0; i < ctx->ev_used / 2; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]) != cudaSuccess) return false;
+        ctx->kernel_ms[ctx->ev_class[i]] += double(ms);
+    }
+    ctx->ev_used = 0;
+    ctx->ev_class.clear();
+    return true;
+}
+
+// Enqueue one kernel launch of class `cls`, bracketed by events when profiling.
+template <class F>
+cudaError_t launch(hd_ctx* ctx, int cls, F&& f) {
+    ctx->launches[cls] += 1;
+    if (!ctx->profiling) return f();
+    if (ctx->ev_used + 2 > ctx->ev.size() && !prof_flush(ctx)) return cudaErrorUnknown;
+    cudaError_t e = cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream);
+    if (e != cudaSuccess) return e;
+    e = f();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream);
+    ctx->ev_class.push_back(cls);
+    ctx->ev_used += 2;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hd_default_opts(hd_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(hd_opts));
+    o->precision = HD_FP64;
+    o->lattice = HD_LATTICE_SQUARE;
+    o->trials_per_cell = 0;
+    o->hist_bins = 50;
+    o->hist_dr = 1e-3;
+    o->cell_min = 2.0;
+    o->block_threads = 128;
+}
+
+const char* hd_status_string(hd_status s) {
+    switch (s) {
+        case HD_OK: return "ok";
+        case HD_ERR_ARG: return "invalid argument";
+        case HD_ERR_CUDA: return "CUDA runtime error";
+        case HD_ERR_OVERFLOW: return "cell capacity overflow";
+        case HD_ERR_TIMEOUT: return "bounded device wait timed out";
+        case HD_ERR_REACH: return "measurement stencil exceeds the box";
+        case HD_ERR_STATE: return "context in sticky error state";
+    }
+    return "unknown status";
+}
+
+hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double* eta, double sigma,
+                        const double* delta, const uint64_t* seed, const hd_opts* opts_in) {
+    if (!out) return HD_ERR_ARG;
+    *out = nullptr;
+    if (R < 1 || !N || !eta || !delta || !seed) return HD_ERR_ARG;
+    hd_opts o;
+    hd_default_opts(&o);
+    if (opts_in) {
+        o.precision = opts_in->precision;
+        o.lattice = opts_in->lattice;
+        o.trials_per_cell = opts_in->trials_per_cell;
+        if (opts_in->hist_bins > 0) o.hist_bins = opts_in->hist_bins;
+        if (opts_in->hist_dr > 0.0) o.hist_dr = opts_in->hist_dr;
+        if (opts_in->cell_min > 0.0) o.cell_min = opts_in->cell_min;
+        if (opts_in->block_threads > 0) o.block_threads = opts_in->block_threads;
+    }
+    if (o.precision != HD_FP64 && o.precision != HD_FIXED32) return HD_ERR_ARG;
+    if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
+    if (!(o.cell_min >= 2.0) || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
+    if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
+
+    std::vector<Plan> plans(static_cast<size_t>(R));
+    int cap = 4;
+    for (int r = 0; r < R; ++r) {
+        const hd_status s = plan_replica(N[r], eta[r], sigma, delta[r], seed[r], o, plans[size_t(r)]);
+        if (s != HD_OK) return s;
+        cap = std::max(cap, plans[size_t(r)].cap);
+    }
+    cap = cap <= 4 ? 4 : 9;
+
+    hd_ctx* ctx = new (std::nothrow) hd_ctx();
+    if (!ctx) return HD_ERR_ARG;
+    ctx->R = R;
+    ctx->fixed = o.precision == HD_FIXED32;
+    ctx->cap = cap;
+    ctx->K = o.hist_bins;
+    ctx->lattice = o.lattice;
+    ctx->threads = o.block_threads;
+    ctx->sigma = sigma;
+    ctx->sweeps.assign(size_t(R), 0);
+    const int64_t DR = std::llround(o.hist_dr * kFx);
+    if (ctx->fixed && DR < 1) {
+        delete ctx;
+        return HD_ERR_ARG;
+    }
+    int64_t cell_off = 0, id_off = 0;
+    int blk_cell = 0, blk_act = 0;
+    for (int r = 0; r < R; ++r) {
+        Rep rep = plans[size_t(r)].rep;
+        rep.cell_off = cell_off;
+        rep.id_off = id_off;
+        rep.blk_cell = blk_cell;
+        rep.blk_act = blk_act;
+        const int64_t ncell = int64_t(rep.m) * rep.m;
+        const int64_t nact = int64_t(rep.hm) * rep.hm;
+        cell_off += ncell;
+        id_off += rep.N;
+        blk_cell += int((ncell + ctx->threads - 1) / ctx->threads);
+        blk_act += int((nact + ctx->threads - 1) / ctx->threads);
+        if (ctx->fixed) {
+            rep.dr = double(DR) / kFx;
+            rep.hist_R = int((((int64_t(1) << 25) + int64_t(ctx->K) * DR)) / rep.W) + 1;
+        } else {
+            rep.dr = o.hist_dr;
+            rep.hist_R = int(std::floor((2.0 + double(ctx->K) * o.hist_dr) / rep.w)) + 1;
+        }
+        ctx->reps.push_back(rep);
+        ctx->nlat.push_back(plans[size_t(r)].nlat);
+    }
+    ctx->Ctot = cell_off;
+    ctx->Ntot = id_off;
+    ctx->blocks_cell = blk_cell;
+    ctx->blocks_act = blk_act;
+
+    const size_t slots = size_t(ctx->Ctot) * cap;
+    bool ok = dev_alloc(ctx, &ctx->reps_d, size_t(R));
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = ok && dev_alloc(ctx, &ctx->buf[b].cnt, size_t(ctx->Ctot));
+        ok = ok && dev_alloc(ctx, &ctx->buf[b].pid, slots);
+        if (ctx->fixed) {
+            int2* p = nullptr;
+            ok = ok && dev_alloc(ctx, &p, slots);
+            ctx->buf[b].pos = p;
+        } else {
+            double2* p = nullptr;
+            ok = ok && dev_alloc(ctx, &p, slots);
+            ctx->buf[b].pos = p;
+        }
+    }
+    ok = ok && dev_alloc(ctx, &ctx->table, size_t(R) * (hd::kMaxChunk + 1));
+    ok = ok && dev_alloc(ctx, &ctx->frame, size_t(R));
+    ok = ok && dev_alloc(ctx, &ctx->sweep_ctr, size_t(R));
+    ok = ok && dev_alloc(ctx, &ctx->counters, size_t(2 * R));
+    ok = ok && dev_alloc(ctx, &ctx->err, 1);
+    ok = ok && dev_alloc(ctx, &ctx->hist, size_t(R) * ctx->K);
+    ok = ok && dev_alloc(ctx, &ctx->edges, size_t(ctx->K + 1));
+    ok = ok && dev_alloc(ctx, &ctx->edgesF, size_t(ctx->K + 1));
+    ok = ok && dev_alloc(ctx, &ctx->fit, size_t(4 * R));
+    ok = ok && dev_alloc(ctx, &ctx->psi_local, size_t(ctx->Ntot));
+    ok = ok && dev_alloc(ctx, &ctx->psi_part, size_t(ctx->blocks_cell));
+    ok = ok && dev_alloc(ctx, &ctx->psi_res, size_t(2 * R));
+    ok = ok && dev_alloc(ctx, &ctx->xy, size_t(2 * ctx->Ntot));
+    if (!ok) {
+        free_ctx(ctx);
+        return HD_ERR_CUDA;
+    }
+    // squared bin edges: FP64 (2 + k dr)^2, fixed (2^25 + k DR)^2
+    std::vector<double> e(size_t(ctx->K + 1));
+    std::vector<long long> ef(size_t(ctx->K + 1));
+    for (int k = 0; k <= ctx->K; ++k) {
+        const double x = 2.0 + double(k) * o.hist_dr;
+        e[size_t(k)] = x * x;
+        const long long xf = (1LL << 25) + (long long)k * DR;
+        ef[size_t(k)] = xf * xf;
+    }
+    bool cu = cudaMemcpy(ctx->reps_d, ctx->reps.data(), sizeof(Rep) * size_t(R), cudaMemcpyHostToDevice) == cudaSuccess;
+    cu = cu && cudaMemcpy(ctx->edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    cu = cu && cudaMemcpy(ctx->edgesF, ef.data(), ef.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->sweep_ctr, 0, sizeof(uint64_t) * size_t(R)) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * size_t(2 * R)) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot)) == cudaSuccess;
+    if (!cu) {
+        free_ctx(ctx);
+        return HD_ERR_CUDA;
+    }
+
+    // initial lattice (square, or odd rows shifted by half a spacing)
+    HostCells h;
+    host_cells_init(ctx, h);
+    for (int r = 0; r < R; ++r) {
+        const Rep& rep = ctx->reps[size_t(r)];
+        const int64_t n = ctx->nlat[size_t(r)];
+        for (int64_t k = 0; k < rep.N; ++k) {
+            const int64_t row = k / n, col = k % n;
+            int64_t numx = 2 * col + 1 + ((ctx->lattice == HD_LATTICE_TRIANGULAR && (row & 1)) ? 1 : 0);
+            if (numx >= 2 * n) numx -= 2 * n;
+            const int64_t numy = 2 * row + 1;
+            double x = 0.0, y = 0.0;
+            int64_t X = 0, Y = 0;
+            if (ctx->fixed) {
+                X = (numx * rep.LF) / (2 * n);
+                Y = (numy * rep.LF) / (2 * n);
+            } else {
+                x = (double(numx) * rep.L) / double(2 * n);
+                y = (double(numy) * rep.L) / double(2 * n);
+            }
+            if (!bin_disk(ctx, rep, h, k, x, y, X, Y)) {
+                free_ctx(ctx);
+                return HD_ERR_OVERFLOW;
+            }
+        }
+    }
+    if (upload_cells(ctx, h) != HD_OK) {
+        free_ctx(ctx);
+        return HD_ERR_CUDA;
+    }
+    *out = ctx;
+    return HD_OK;
+}
+
+hd_status hd_init(hd_ctx** out, int64_t N, double eta, double sigma, double delta, uint64_t seed,
+                  const hd_opts* opts) {
+    return hd_batch_init(out, 1, &N, &eta, sigma, &delta, &seed, opts);
+}
+
+hd_status hd_destroy(hd_ctx* ctx) {
+    if (!ctx) return HD_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+    return HD_OK;
+}
+
+hd_status hd_set_stream(hd_ctx* ctx, void* stream) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return HD_OK;
+}
+
+hd_status hd_sweep(hd_ctx* ctx, int64_t n) {
+    if (!ctx || n < 0) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const hd::LaunchCfg c = ctx->cfg();
+    int64_t left = n;
+    while (left > 0) {
+        const int nc = int(std::min<int64_t>(left, hd::kMaxChunk));
+        HD_CK(ctx, launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); }));
+        for (int j = 1; j <= nc; ++j) {
+            HD_CK(ctx, launch(ctx, HD_K_REBUILD, [&] {
+                return hd::launch_rebuild(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->err);
+            }));
+            ctx->cur ^= 1;
+            for (int p = 0; p < 4; ++p)
+                HD_CK(ctx, launch(ctx, HD_K_PASS, [&] { return hd::launch_pass(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters); }));
+        }
+        left -= nc;
+    }
+    for (auto& s : ctx->sweeps) s += n;
+    return HD_OK;
+}
+
+hd_status hd_pressure(hd_ctx* ctx, double* betaP_over_rho, double* g_contact, uint64_t* hist) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    for (const Rep& r : ctx->reps)
+        if (2 * r.hist_R + 1 > r.m) return HD_ERR_REACH;
+    const hd::LaunchCfg c = ctx->cfg();
+    HD_CK(ctx, cudaMemsetAsync(ctx->hist, 0, sizeof(unsigned long long) * size_t(ctx->R) * ctx->K, ctx->stream));
+    hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF};
+    HD_CK(ctx, launch(ctx, HD_K_HIST, [&] { return hd::launch_hist(c, h, ctx->buf[ctx->cur], ctx->hist); }));
+    HD_CK(ctx, launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->hist, ctx->fit); }));
+    std::vector<double> res(size_t(4 * ctx->R));
+    HD_CK(ctx, cudaMemcpyAsync(res.data(), ctx->fit, res.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (hist)
+        HD_CK(ctx, cudaMemcpyAsync(hist, ctx->hist, sizeof(unsigned long long) * size_t(ctx->R) * ctx->K,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const hd_status f = check_flags(ctx);
+    if (f != HD_OK) return f;
+    for (int r = 0; r < ctx->R; ++r) {
+        if (betaP_over_rho) betaP_over_rho[r] = res[size_t(4 * r)];
+        if (g_contact) g_contact[r] = res[size_t(4 * r + 1)];
+    }
+    return HD_OK;
+}
+
+hd_status hd_psi6(hd_ctx* ctx, double* re, double* im, double* local) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const hd::LaunchCfg c = ctx->cfg();
+    HD_CK(ctx, launch(ctx, HD_K_PSI6, [&] {
+        return hd::launch_psi6(c, ctx->buf[ctx->cur], local ? ctx->psi_local : nullptr, ctx->psi_part, ctx->err);
+    }));
+    HD_CK(ctx, launch(ctx, HD_K_PSI6_REDUCE, [&] { return hd::launch_psi6_reduce(c, ctx->psi_part, ctx->psi_res); }));
+    std::vector<double> res(size_t(2 * ctx->R));
+    HD_CK(ctx, cudaMemcpyAsync(res.data(), ctx->psi_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    if (local)
+        HD_CK(ctx, cudaMemcpyAsync(local, ctx->psi_local, sizeof(double2) * size_t(ctx->Ntot), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const hd_status f = check_flags(ctx);
+    if (f != HD_OK) return f;
+    for (int r = 0; r < ctx->R; ++r) {
+        if (re) re[r] = res[size_t(2 * r)];
+        if (im) im[r] = res[size_t(2 * r + 1)];
+    }
+    return HD_OK;
+}
+
+hd_status hd_positions_device(hd_ctx* ctx, double* xy_device) {
+    if (!ctx || !xy_device) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] {
+        return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], xy_device);
+    }));
+    return HD_OK;
+}
+
+hd_status hd_positions(hd_ctx* ctx, double* xy) {
+    if (!ctx || !xy) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] { return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], ctx->xy); }));
+    HD_CK(ctx, cudaMemcpyAsync(xy, ctx->xy, sizeof(double) * 2 * size_t(ctx->Ntot), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx);
+}
+
+hd_status hd_set_positions(hd_ctx* ctx, const double* xy) {
+    if (!ctx || !xy) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HostCells h;
+    host_cells_init(ctx, h);
+    for (int r = 0; r < ctx->R; ++r) {
+        const Rep& rep = ctx->reps[size_t(r)];
+        for (int64_t k = 0; k < rep.N; ++k) {
+            const double px = xy[2 * (rep.id_off + k)] / ctx->sigma;
+            const double py = xy[2 * (rep.id_off + k) + 1] / ctx->sigma;
+            if (!std::isfinite(px) || !std::isfinite(py)) return HD_ERR_ARG;
+            double x = 0.0, y = 0.0;
+            int64_t X = 0, Y = 0;
+            if (ctx->fixed) {
+                X = std::llround(px * kFx) % rep.LF;
+                Y = std::llround(py * kFx) % rep.LF;
+                if (X < 0) X += rep.LF;
+                if (Y < 0) Y += rep.LF;
+            } else {
+                x = std::fmod(px, rep.L);
+                y = std::fmod(py, rep.L);
+                if (x < 0.0) x += rep.L;
+                if (y < 0.0) y += rep.L;
+                if (x >= rep.L) x = 0.0;
+                if (y >= rep.L) y = 0.0;
+            }
+            if (!bin_disk(ctx, rep, h, k, x, y, X, Y)) return HD_ERR_OVERFLOW;
+        }
+    }
+    return upload_cells(ctx, h);
+}
+
+hd_status hd_stats(hd_ctx* ctx, uint64_t* attempts, uint64_t* accepts) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    std::vector<unsigned long long> c(size_t(2 * ctx->R));
+    HD_CK(ctx, cudaMemcpyAsync(c.data(), ctx->counters, c.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < ctx->R; ++r) {
+        if (attempts) attempts[r] = c[size_t(2 * r)];
+        if (accepts) accepts[r] = c[size_t(2 * r + 1)];
+    }
+    return check_flags(ctx);
+}
+
+hd_status hd_get_geometry(hd_ctx* ctx, int32_t r, hd_geometry* g) {
+    if (!ctx || !g || r < 0 || r >= ctx->R) return HD_ERR_ARG;
+    const Rep& rep = ctx->reps[size_t(r)];
+    g->N = rep.N;
+    g->m = rep.m;
+    g->capacity = ctx->cap;
+    g->trials_per_cell = rep.nt;
+    g->precision = ctx->fixed ? HD_FIXED32 : HD_FP64;
+    g->hist_bins = ctx->K;
+    g->reserved = 0;
+    g->L = ctx->fixed ? double(rep.LF) / kFx : rep.L;
+    g->w = ctx->fixed ? double(rep.W) / kFx : rep.w;
+    g->delta = ctx->fixed ? double(rep.D) / kFx : rep.delta;
+    g->eta = double(rep.N) * kPi / (g->L * g->L);
+    g->hist_dr = rep.dr;
+    g->sweeps = ctx->sweeps[size_t(r)];
+    return HD_OK;
+}
+
+int32_t hd_replicas(const hd_ctx* ctx) { return ctx ? ctx->R : 0; }
+
+hd_status hd_profile(hd_ctx* ctx, int32_t enable) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    if (!prof_flush(ctx)) return fail_cuda(ctx);
+    if (enable) {
+        if (ctx->ev.empty()) {
+            ctx->ev.resize(8192);
+            for (auto& e : ctx->ev)
+                if (cudaEventCreate(&e) != cudaSuccess) return fail_cuda(ctx);
+        }
+        for (int k = 0; k < HD_KERNEL_CLASSES; ++k) {
+            ctx->kernel_ms[k] = 0.0;
+            ctx->launches[k] = 0;
+        }
+    }
+    ctx->profiling = enable != 0;
+    return HD_OK;
+}
+
+hd_status hd_kernel_times(hd_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    if (!prof_flush(ctx)) return fail_cuda(ctx);
+    for (int k = 0; k < HD_KERNEL_CLASSES; ++k) {
+        if (ms) ms[k] = ctx->kernel_ms[k];
+        if (launches) launches[k] = ctx->launches[k];
+    }
+    return HD_OK;
+}
+
+}  // extern "C"

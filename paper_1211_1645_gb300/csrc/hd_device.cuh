@@ -1,0 +1,130 @@
+// hd_device.cuh -- device-side building blocks of the MPMC hard-disk kernels:
+// the counter-based generator, per-replica constants, the per-sweep draw
+// table and small helpers shared by the sweep and measurement kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hd {
+
+// Fourth Philox counter word: keeps the draw streams of one sweep disjoint.
+constexpr uint32_t kTagSweep = 1u;    // grid shift and colour order of a sweep
+constexpr uint32_t kTagShuffle = 2u;  // occupant shuffle of one cell
+constexpr uint32_t kTagTrial = 3u;    // one trial move of one cell
+
+constexpr int kMaxChunk = 256;        // sweeps per draw table
+constexpr int64_t kFxDiam2 = int64_t(1) << 50;  // (2 sigma)^2 in (2^-24 sigma)^2
+
+// Constants of one replica (one independent chain).  Read-only in kernels.
+struct Rep {
+    int64_t N;
+    int64_t cell_off;   // first cell of the replica in the concatenated cell arrays
+    int64_t id_off;     // first disk of the replica in the global id order
+    int64_t LF;         // fixed point: box side m * W
+    int32_t m, hm;      // cells per side, m / 2
+    int32_t nt;         // trial moves per occupied active cell per pass
+    int32_t blk_cell;   // first block of the replica in whole-cell grids
+    int32_t blk_act;    // first block of the replica in active-cell grids
+    int32_t W, D;       // fixed point: cell side, maximum step (units 2^-24 sigma)
+    int32_t hist_R;     // cell reach of the contact histogram
+    double w, w_below;  // FP64 cell side and the largest double below it
+    double L, delta;    // FP64 box side and maximum step (sigma units)
+    double sigma;       // disk radius (output scale)
+    double dr;          // realised histogram bin width (sigma units)
+    uint32_t key0, key1;
+};
+
+// Draws of one sweep: the shift of its cell frame and its colour order.
+struct Frame {
+    double sx, sy;   // FP64 shift in [0, w)
+    int32_t Sx, Sy;  // fixed-point shift in [0, W)
+    uint32_t sweep;  // first Philox counter word of the sweep
+    uint32_t perm;   // colour of pass p = (perm >> 2p) & 3
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 multiply-xor
+// bijection with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t y0 = hi1 ^ c1 ^ k0;
+        const uint32_t y2 = hi0 ^ c3 ^ k1;
+        c0 = y0;
+        c1 = lo1;
+        c2 = y2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// floor(word * n / 2^32): an integer in [0, n).
+__device__ __forceinline__ uint32_t bounded(uint32_t word, uint32_t n) { return __umulhi(word, n); }
+
+__device__ __forceinline__ int wrap_cell(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
+
+// Replica owning block `blk`, given per-replica first blocks (ascending).
+template <bool ACT>
+__device__ __forceinline__ int find_rep(const Rep* __restrict__ reps, int R, int blk) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int start = ACT ? reps[mid].blk_act : reps[mid].blk_cell;
+        if (start <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Symmetric FP64 step in (-delta, delta) from two 32-bit words: a 53-bit
+// integer k gives (2k + 1 - 2^53) * 2^-53, a set symmetric about zero.
+__device__ __forceinline__ double step_fp64(uint32_t hi, uint32_t lo, double delta) {
+    const uint64_t k = (uint64_t(hi >> 6) << 27) | uint64_t(lo >> 5);
+    const int64_t v = int64_t(2 * k + 1) - (int64_t(1) << 53);
+    return __dmul_rn(delta, double(v)) * 0x1p-53;
+}
+
+// Move one coordinate of one disk into the next cell frame (FP64).  d is the
+// old shift minus the new one, |d| < w.  Edge cases at the last ulp are
+// resolved toward staying inside [0, w).
+__device__ __forceinline__ void frame_change_fp64(double d, double w, double w_below, int m, int c,
+                                                  double u, int& c_out, double& u_out) {
+    double t = __dadd_rn(u, d);
+    if (t < 0.0) {
+        const double v = __dadd_rn(t, w);
+        if (v < w) {
+            c -= 1;
+            t = v;
+        } else {
+            t = 0.0;
+        }
+    } else if (t >= w) {
+        t = __dsub_rn(t, w);
+        c += 1;
+        if (t >= w) t = w_below;
+    }
+    c_out = wrap_cell(c, m);
+    u_out = t;
+}
+
+__device__ __forceinline__ void frame_change_fixed(int32_t d, int32_t W, int m, int c, int32_t u,
+                                                   int& c_out, int32_t& u_out) {
+    int32_t t = u + d;
+    if (t < 0) {
+        t += W;
+        c -= 1;
+    } else if (t >= W) {
+        t -= W;
+        c += 1;
+    }
+    c_out = wrap_cell(c, m);
+    u_out = t;
+}
+
+}  // namespace hd

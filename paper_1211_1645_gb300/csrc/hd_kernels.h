@@ -1,0 +1,48 @@
+// hd_kernels.h -- host-side launch interface of the MPMC kernels.  Each
+// launcher enqueues one kernel on `stream` and returns the launch status.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hd_device.cuh"
+
+namespace hd {
+
+// Device buffers of one cell-list generation (ping-pong pair in the context).
+struct CellBufs {
+    uint8_t* cnt;   // [cells] occupancy
+    void* pos;      // [cells * cap] double2 (FP64) or int2 (fixed) cell offsets
+    int32_t* pid;   // [cells * cap] disk id within the replica
+};
+
+struct LaunchCfg {
+    const Rep* reps;   // device array [R]
+    int R;
+    int cap;           // 4 or 9
+    bool fixed;        // fixed-point form
+    int threads;       // threads per block
+    int blocks_cell;   // whole-cell grid size (all replicas)
+    int blocks_act;    // active-cell grid size (all replicas)
+    cudaStream_t stream;
+};
+
+cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t* sweep_ctr, int nchunk);
+cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,
+                           int* err);
+cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
+                        unsigned long long* counters);
+cudaError_t launch_positions(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy);
+
+// Measurement.
+struct HistCfg {
+    int K;
+    const double* edges;      // [K + 1] FP64 squared bin edges
+    const long long* edgesF;  // [K + 1] fixed-point squared bin edges
+};
+cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist);
+cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res);
+cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err);
+cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res);
+
+}  // namespace hd

@@ -1,0 +1,427 @@
+// hd_measure.cu -- measurements on the MPMC cell frame (Engel et al.,
+// arXiv:1211.1645): the contact-shell pair histogram and the contact-value
+// pressure (Sec. II.C.1, Eqs. 2 and 4), and the local / global
+// bond-orientational order psi_6 (Sec. III, Eq. 8).
+//
+// Pair vectors are formed in the cell frame: for disks i and j whose cells
+// differ by (dcx, dcy), r = (u_j + dcx * w) - u_i, which is exact in the
+// fixed-point form and has one fixed rounding order in FP64.
+#include <type_traits>
+
+#include "hd_kernels.h"
+
+namespace hd {
+
+template <bool FIX>
+using P2 = std::conditional_t<FIX, int2, double2>;
+
+constexpr int kMaxFitBins = 512;
+
+// ---------------------------------------------------------------------------
+// Contact-shell histogram: unordered pairs with 2 <= r < 2 + K dr, binned by
+// comparing r^2 with squared bin edges; each pair is seen from its lower id.
+// One thread per cell scans the (2R+1)^2 stencil; counts gather in a shared
+// histogram and are flushed with one atomic per non-empty bin and block.
+// ---------------------------------------------------------------------------
+template <bool FIX, int CAP>
+__global__ void __launch_bounds__(256)
+k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ edges,
+       const long long* __restrict__ edgesF, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
+       const int32_t* __restrict__ pid, unsigned long long* __restrict__ hist) {
+    extern __shared__ unsigned int s_bins[];
+    for (int b = threadIdx.x; b < K; b += blockDim.x) s_bins[b] = 0u;
+    __syncthreads();
+    const int r = find_rep<false>(reps, R, blockIdx.x);
+    const Rep& rep = reps[r];
+    const int m = rep.m;
+    const int64_t c = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
+    if (c < int64_t(m) * m) {
+        const int cx = int(c % m), cy = int(c / m);
+        const int64_t cell = rep.cell_off + c;
+        const int n = cnt[cell];
+        const int RR = rep.hist_R;
+        const double e0 = edges[0], eK = edges[K];
+        const long long f0 = edgesF[0], fK = edgesF[K];
+        for (int k = 0; k < n; ++k) {
+            const P2<FIX> me = pos[cell * CAP + k];
+            const int32_t idme = pid[cell * CAP + k];
+            for (int dcy = -RR; dcy <= RR; ++dcy) {
+                for (int dcx = -RR; dcx <= RR; ++dcx) {
+                    const int64_t nc = rep.cell_off + int64_t(wrap_cell(cy + dcy, m)) * m + wrap_cell(cx + dcx, m);
+                    const int nn = cnt[nc];
+                    for (int q = 0; q < nn; ++q) {
+                        const int32_t idq = pid[nc * CAP + q];
+                        if (idq <= idme) continue;
+                        const P2<FIX> o = pos[nc * CAP + q];
+                        int bin;
+                        if constexpr (FIX) {
+                            const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
+                            const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
+                            const long long r2 = rx * rx + ry * ry;
+                            if (r2 < f0 || r2 >= fK) continue;
+                            int lo = 0, hi = K - 1;  // largest k with edgesF[k] <= r2
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (__ldg(&edgesF[mid]) <= r2) lo = mid; else hi = mid - 1;
+                            }
+                            bin = lo;
+                        } else {
+                            const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
+                            const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
+                            const double r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
+                            if (r2 < e0 || r2 >= eK) continue;
+                            int lo = 0, hi = K - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (__ldg(&edges[mid]) <= r2) lo = mid; else hi = mid - 1;
+                            }
+                            bin = lo;
+                        }
+                        atomicAdd(&s_bins[bin], 1u);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < K; b += blockDim.x)
+        if (s_bins[b]) atomicAdd(&hist[size_t(r) * K + b], (unsigned long long)s_bins[b]);
+}
+
+// ---------------------------------------------------------------------------
+// g(r) normalisation (Eq. 2, p = N^2 / 2), least-squares quartic in
+// t = (r - 2 sigma) / (K dr) by Householder QR, value at contact, and the
+// contact-value pressure (Eq. 4).  One block per replica, one thread works.
+// res[4r + 0..3] = beta P / rho, g(2 sigma+), P* = beta P (2 sigma)^2, eta.
+// ---------------------------------------------------------------------------
+__global__ void k_fit(const Rep* __restrict__ reps, int K, const unsigned long long* __restrict__ hist,
+                      double* __restrict__ res) {
+    __shared__ double A[kMaxFitBins * 5];
+    __shared__ double b[kMaxFitBins];
+    if (threadIdx.x != 0) return;
+    const int r = blockIdx.x;
+    const Rep& rep = reps[r];
+    const double PI = 3.14159265358979323846;
+    const double V = __dmul_rn(rep.L, rep.L);
+    const double p = __dmul_rn(__dmul_rn(double(rep.N), double(rep.N)), 0.5);
+    const double dr = rep.dr;
+    for (int k = 0; k < K; ++k) {
+        const double rk = __dadd_rn(2.0, __dmul_rn(__dadd_rn(double(k), 0.5), dr));
+        const double shell = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, PI), rk), dr), V);
+        b[k] = __ddiv_rn(__ddiv_rn(double(hist[size_t(r) * K + k]), p), shell);
+        const double t = __ddiv_rn(__dadd_rn(double(k), 0.5), double(K));
+        double tp = 1.0;
+        for (int q = 0; q < 5; ++q) {
+            A[k * 5 + q] = tp;
+            tp = __dmul_rn(tp, t);
+        }
+    }
+    // Householder triangularisation of the K x 5 design matrix, applied to b
+    for (int j = 0; j < 5; ++j) {
+        double nrm2 = 0.0;
+        for (int i = j; i < K; ++i) nrm2 = __dadd_rn(nrm2, __dmul_rn(A[i * 5 + j], A[i * 5 + j]));
+        const double nrm = sqrt(nrm2);
+        if (nrm == 0.0) continue;
+        const double alpha = A[j * 5 + j] > 0.0 ? -nrm : nrm;
+        const double v0 = __dsub_rn(A[j * 5 + j], alpha);
+        const double vtv = __dadd_rn(__dsub_rn(nrm2, __dmul_rn(A[j * 5 + j], A[j * 5 + j])), __dmul_rn(v0, v0));
+        A[j * 5 + j] = v0;  // v = (v0, A[j+1.., j])
+        for (int q = j + 1; q < 5; ++q) {
+            double d = 0.0;
+            for (int i = j; i < K; ++i) d = __dadd_rn(d, __dmul_rn(A[i * 5 + j], A[i * 5 + q]));
+            const double s = __ddiv_rn(__dmul_rn(2.0, d), vtv);
+            for (int i = j; i < K; ++i) A[i * 5 + q] = __dsub_rn(A[i * 5 + q], __dmul_rn(s, A[i * 5 + j]));
+        }
+        double d = 0.0;
+        for (int i = j; i < K; ++i) d = __dadd_rn(d, __dmul_rn(A[i * 5 + j], b[i]));
+        const double s = __ddiv_rn(__dmul_rn(2.0, d), vtv);
+        for (int i = j; i < K; ++i) b[i] = __dsub_rn(b[i], __dmul_rn(s, A[i * 5 + j]));
+        A[j * 5 + j] = alpha;  // R diagonal; the sub-diagonal of column j is no longer needed
+    }
+    double coef[5];
+    for (int j = 4; j >= 0; --j) {
+        double acc = b[j];
+        for (int q = j + 1; q < 5; ++q) acc = __dsub_rn(acc, __dmul_rn(A[j * 5 + q], coef[q]));
+        coef[j] = __ddiv_rn(acc, A[j * 5 + j]);
+    }
+    const double g0 = coef[0];
+    const double eta = __ddiv_rn(__dmul_rn(double(rep.N), PI), V);
+    const double bp = __dadd_rn(1.0, __dmul_rn(__dmul_rn(2.0, eta), g0));
+    res[4 * r + 0] = bp;
+    res[4 * r + 1] = g0;
+    res[4 * r + 2] = __dmul_rn(__dmul_rn(bp, 4.0), __ddiv_rn(double(rep.N), V));
+    res[4 * r + 3] = eta;
+}
+
+// ---------------------------------------------------------------------------
+// psi_6: six nearest neighbours by (r^2, id) from an expanding ring of cells
+// (first the 5 x 5 stencil, then one ring more while the sixth neighbour is
+// not strictly closer than the nearest point outside the scanned cells).
+// exp(6 i phi) = z^6 / |z|^6, z = rx + i ry, summed in ascending (r^2, id).
+// ---------------------------------------------------------------------------
+template <bool FIX>
+struct Nbr {
+    using Key = std::conditional_t<FIX, long long, double>;
+    Key key[6];
+    int32_t id[6];
+    Key rx[6], ry[6];
+    int n;
+
+    __device__ __forceinline__ void insert(Key k, int32_t i, Key x, Key y) {
+        if (n == 6 && !(k < key[5] || (k == key[5] && i < id[5]))) return;
+        bool done = false;
+        const int top = n < 6 ? n : 5;
+#pragma unroll
+        for (int s = 5; s >= 0; --s) {
+            if (!done && s <= top) {
+                if (s > 0 && (k < key[s - 1] || (k == key[s - 1] && i < id[s - 1]))) {
+                    key[s] = key[s - 1];
+                    id[s] = id[s - 1];
+                    rx[s] = rx[s - 1];
+                    ry[s] = ry[s - 1];
+                } else {
+                    key[s] = k;
+                    id[s] = i;
+                    rx[s] = x;
+                    ry[s] = y;
+                    done = true;
+                }
+            }
+        }
+        if (n < 6) ++n;
+    }
+};
+
+template <bool FIX, int CAP>
+__device__ __forceinline__ void scan_cell(const Rep& rep, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
+                                          const int32_t* __restrict__ pid, int cx, int cy, int dcx, int dcy,
+                                          const P2<FIX>& me, int32_t idme, Nbr<FIX>& nb) {
+    const int m = rep.m;
+    const int64_t nc = rep.cell_off + int64_t(wrap_cell(cy + dcy, m)) * m + wrap_cell(cx + dcx, m);
+    const int nn = cnt[nc];
+    for (int q = 0; q < nn; ++q) {
+        const int32_t idq = pid[nc * CAP + q];
+        if (idq == idme) continue;
+        const P2<FIX> o = pos[nc * CAP + q];
+        if constexpr (FIX) {
+            const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
+            const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
+            nb.insert(rx * rx + ry * ry, idq, rx, ry);
+        } else {
+            const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
+            const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
+            nb.insert(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), idq, rx, ry);
+        }
+    }
+}
+
+template <bool FIX, int CAP>
+__global__ void __launch_bounds__(256)
+k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
+       const int32_t* __restrict__ pid, double2* __restrict__ local, double2* __restrict__ partial,
+       int* __restrict__ err) {
+    const int r = find_rep<false>(reps, R, blockIdx.x);
+    const Rep& rep = reps[r];
+    const int m = rep.m;
+    const int64_t c = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
+    double sr = 0.0, si = 0.0;
+    if (c < int64_t(m) * m) {
+        const int cx = int(c % m), cy = int(c / m);
+        const int64_t cell = rep.cell_off + c;
+        const int n = cnt[cell];
+        int rmax = (m - 1) / 2;
+        if constexpr (FIX) {
+            const int lim = int((int64_t(1) << 31) / rep.W) - 1;
+            if (lim < rmax) rmax = lim;
+        }
+        for (int k = 0; k < n; ++k) {
+            const P2<FIX> me = pos[cell * CAP + k];
+            const int32_t idme = pid[cell * CAP + k];
+            Nbr<FIX> nb;
+            nb.n = 0;
+            bool ok = false;
+            for (int RR = 2; RR <= rmax && !ok; ++RR) {
+                if (RR == 2) {
+                    for (int dcy = -2; dcy <= 2; ++dcy)
+                        for (int dcx = -2; dcx <= 2; ++dcx)
+                            scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, dcx, dcy, me, idme, nb);
+                } else {
+                    for (int e = -RR; e <= RR; ++e) {
+                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, -RR, me, idme, nb);
+                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, RR, me, idme, nb);
+                    }
+                    for (int e = -RR + 1; e <= RR - 1; ++e) {
+                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, -RR, e, me, idme, nb);
+                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, RR, e, me, idme, nb);
+                    }
+                }
+                if (nb.n == 6) {
+                    if constexpr (FIX) {
+                        long long cv = static_cast<long long>(me.x) + static_cast<long long>(RR) * rep.W;
+                        const long long c2 = static_cast<long long>(RR + 1) * rep.W - me.x;
+                        const long long c3 = static_cast<long long>(me.y) + static_cast<long long>(RR) * rep.W;
+                        const long long c4 = static_cast<long long>(RR + 1) * rep.W - me.y;
+                        cv = c2 < cv ? c2 : cv;
+                        cv = c3 < cv ? c3 : cv;
+                        cv = c4 < cv ? c4 : cv;
+                        ok = nb.key[5] < cv * cv;
+                    } else {
+                        double cv = __dadd_rn(me.x, __dmul_rn(double(RR), rep.w));
+                        const double c2 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.x);
+                        const double c3 = __dadd_rn(me.y, __dmul_rn(double(RR), rep.w));
+                        const double c4 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.y);
+                        cv = c2 < cv ? c2 : cv;
+                        cv = c3 < cv ? c3 : cv;
+                        cv = c4 < cv ? c4 : cv;
+                        ok = nb.key[5] < __dmul_rn(cv, cv);
+                    }
+                }
+            }
+            double pre, pim;
+            if (!ok) {
+                atomicOr(err, 2);
+                pre = pim = 0.0;
+            } else if constexpr (FIX) {
+                float fr = 0.0f, fi = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float x = __fmul_rn(__ll2float_rn(nb.rx[q]), 0x1p-24f);
+                    const float y = __fmul_rn(__ll2float_rn(nb.ry[q]), 0x1p-24f);
+                    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y);
+                    const float r2 = __fadd_rn(xx, yy);
+                    const float c2 = __fsub_rn(xx, yy), s2 = __fmul_rn(__fmul_rn(x, y), 2.0f);
+                    const float c4 = __fsub_rn(__fmul_rn(c2, c2), __fmul_rn(s2, s2));
+                    const float s4 = __fmul_rn(__fmul_rn(c2, s2), 2.0f);
+                    const float c6 = __fsub_rn(__fmul_rn(c4, c2), __fmul_rn(s4, s2));
+                    const float s6 = __fadd_rn(__fmul_rn(c4, s2), __fmul_rn(s4, c2));
+                    const float r6 = __fmul_rn(__fmul_rn(r2, r2), r2);
+                    fr = __fadd_rn(fr, __fdiv_rn(c6, r6));
+                    fi = __fadd_rn(fi, __fdiv_rn(s6, r6));
+                }
+                pre = double(__fdiv_rn(fr, 6.0f));
+                pim = double(__fdiv_rn(fi, 6.0f));
+            } else {
+                double dr_ = 0.0, di = 0.0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const double x = nb.rx[q], y = nb.ry[q];
+                    const double xx = __dmul_rn(x, x), yy = __dmul_rn(y, y);
+                    const double r2 = __dadd_rn(xx, yy);
+                    const double c2 = __dsub_rn(xx, yy), s2 = __dmul_rn(__dmul_rn(x, y), 2.0);
+                    const double c4 = __dsub_rn(__dmul_rn(c2, c2), __dmul_rn(s2, s2));
+                    const double s4 = __dmul_rn(__dmul_rn(c2, s2), 2.0);
+                    const double c6 = __dsub_rn(__dmul_rn(c4, c2), __dmul_rn(s4, s2));
+                    const double s6 = __dadd_rn(__dmul_rn(c4, s2), __dmul_rn(s4, c2));
+                    const double r6 = __dmul_rn(__dmul_rn(r2, r2), r2);
+                    dr_ = __dadd_rn(dr_, __ddiv_rn(c6, r6));
+                    di = __dadd_rn(di, __ddiv_rn(s6, r6));
+                }
+                pre = __ddiv_rn(dr_, 6.0);
+                pim = __ddiv_rn(di, 6.0);
+            }
+            if (local) local[rep.id_off + idme] = make_double2(pre, pim);
+            sr += pre;
+            si += pim;
+        }
+    }
+    // fixed-order block reduction of the per-thread sums
+    __shared__ double s_re[32], s_im[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, off);
+        si += __shfl_down_sync(0xffffffffu, si, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_re[warp] = sr;
+        s_im[warp] = si;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+            tr += s_re[w];
+            ti += s_im[w];
+        }
+        partial[blockIdx.x] = make_double2(tr, ti);
+    }
+}
+
+// Sum the block partials of each replica in a fixed order; Psi_6 = sum / N.
+__global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_total,
+                              const double2* __restrict__ partial, double* __restrict__ res) {
+    const int r = blockIdx.x;
+    const Rep& rep = reps[r];
+    const int b0 = rep.blk_cell;
+    const int b1 = (r + 1 < R) ? reps[r + 1].blk_cell : blocks_total;
+    double sr = 0.0, si = 0.0;
+    for (int b = b0 + int(threadIdx.x); b < b1; b += blockDim.x) {
+        sr += partial[b].x;
+        si += partial[b].y;
+    }
+    __shared__ double s_re[1024], s_im[1024];
+    s_re[threadIdx.x] = sr;
+    s_im[threadIdx.x] = si;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (int(threadIdx.x) < s) {
+            s_re[threadIdx.x] += s_re[threadIdx.x + s];
+            s_im[threadIdx.x] += s_im[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        res[2 * r] = s_re[0] / double(rep.N);
+        res[2 * r + 1] = s_im[0] / double(rep.N);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <bool FIX, int CAP>
+static void hist_t(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
+    k_hist<FIX, CAP><<<c.blocks_cell, c.threads, size_t(h.K) * sizeof(unsigned int), c.stream>>>(
+        c.reps, c.R, h.K, h.edges, h.edgesF, cells.cnt, (const P2<FIX>*)cells.pos, cells.pid, hist);
+}
+
+cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
+    if (c.fixed) {
+        if (c.cap == 4) hist_t<true, 4>(c, h, cells, hist);
+        else hist_t<true, 9>(c, h, cells, hist);
+    } else {
+        if (c.cap == 4) hist_t<false, 4>(c, h, cells, hist);
+        else hist_t<false, 9>(c, h, cells, hist);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res) {
+    if (K > kMaxFitBins) return cudaErrorInvalidValue;
+    k_fit<<<c.R, 32, 0, c.stream>>>(c.reps, K, hist, res);
+    return cudaGetLastError();
+}
+
+template <bool FIX, int CAP>
+static void psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
+    k_psi6<FIX, CAP><<<c.blocks_cell, c.threads, 0, c.stream>>>(c.reps, c.R, cells.cnt, (const P2<FIX>*)cells.pos,
+                                                                  cells.pid, local, partial, err);
+}
+
+cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
+    if (c.fixed) {
+        if (c.cap == 4) psi6_t<true, 4>(c, cells, local, partial, err);
+        else psi6_t<true, 9>(c, cells, local, partial, err);
+    } else {
+        if (c.cap == 4) psi6_t<false, 4>(c, cells, local, partial, err);
+        else psi6_t<false, 9>(c, cells, local, partial, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res) {
+    k_psi6_reduce<<<c.R, 256, 0, c.stream>>>(c.reps, c.R, c.blocks_cell, partial, res);
+    return cudaGetLastError();
+}
+
+}  // namespace hd

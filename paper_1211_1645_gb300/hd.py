@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C ABI in include/hd.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_build/libhd.so``; there is
+no computational fallback.  If the library is missing or cannot be loaded the
+import of a function raises ``HDError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HD_OK, HD_ERR_ARG, HD_ERR_CUDA, HD_ERR_OVERFLOW, HD_ERR_TIMEOUT, HD_ERR_REACH, HD_ERR_STATE = range(7)
+HD_FP64, HD_FIXED32 = 0, 1
+HD_LATTICE_SQUARE, HD_LATTICE_TRIANGULAR = 0, 1
+
+PRECISIONS = {"fp64": HD_FP64, "fixed": HD_FIXED32}
+LATTICES = {"square": HD_LATTICE_SQUARE, "triangular": HD_LATTICE_TRIANGULAR}
+
+
+class HDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status) if _lib_or_none() else status} (status {status})")
+
+
+class hd_opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("lattice", ctypes.c_int32),
+        ("trials_per_cell", ctypes.c_int32),
+        ("hist_bins", ctypes.c_int32),
+        ("hist_dr", ctypes.c_double),
+        ("cell_min", ctypes.c_double),
+        ("block_threads", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class hd_geometry(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64),
+        ("m", ctypes.c_int32),
+        ("capacity", ctypes.c_int32),
+        ("trials_per_cell", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("hist_bins", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("L", ctypes.c_double),
+        ("w", ctypes.c_double),
+        ("delta", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("hist_dr", ctypes.c_double),
+        ("sweeps", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load(path: str | None = None):
+    """Load libhd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        so = path or _build.build()
+        if not os.path.exists(so):
+            raise HDError(HD_ERR_CUDA, f"libhd.so not found at {so}")
+        lib = ctypes.CDLL(so)
+        c = ctypes
+        P = c.c_void_p
+        S = c.c_int
+        sig = {
+            "hd_default_opts": (None, [c.POINTER(hd_opts)]),
+            "hd_status_string": (c.c_char_p, [S]),
+            "hd_init": (S, [c.POINTER(P), c.c_int64, c.c_double, c.c_double, c.c_double, c.c_uint64,
+                            c.POINTER(hd_opts)]),
+            "hd_batch_init": (S, [c.POINTER(P), c.c_int32, P, P, c.c_double, P, P, c.POINTER(hd_opts)]),
+            "hd_destroy": (S, [P]),
+            "hd_set_stream": (S, [P, P]),
+            "hd_sweep": (S, [P, c.c_int64]),
+            "hd_pressure": (S, [P, P, P, P]),
+            "hd_psi6": (S, [P, P, P, P]),
+            "hd_positions": (S, [P, P]),
+            "hd_positions_device": (S, [P, P]),
+            "hd_set_positions": (S, [P, P]),
+            "hd_stats": (S, [P, P, P]),
+            "hd_get_geometry": (S, [P, c.c_int32, c.POINTER(hd_geometry)]),
+            "hd_replicas": (c.c_int32, [P]),
+            "hd_profile": (S, [P, c.c_int32]),
+            "hd_kernel_times": (S, [P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(s: int) -> str:
+    return load().hd_status_string(int(s)).decode()
+
+
+def _check(st: int, where: str):
+    if st != HD_OK:
+        raise HDError(st, where)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def hd_default_opts() -> hd_opts:
+    o = hd_opts()
+    load().hd_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=50, hist_dr=1e-3,
+              cell_min=2.0, block_threads=128) -> hd_opts:
+    o = hd_default_opts()
+    o.precision = PRECISIONS.get(precision, precision)
+    o.lattice = LATTICES.get(lattice, lattice)
+    o.trials_per_cell = int(trials_per_cell)
+    o.hist_bins = int(hist_bins)
+    o.hist_dr = float(hist_dr)
+    o.cell_min = float(cell_min)
+    o.block_threads = int(block_threads)
+    return o
+
+
+def hd_init(N, eta, sigma, delta, seed, opts: hd_opts | None = None):
+    h = ctypes.c_void_p()
+    st = load().hd_init(ctypes.byref(h), int(N), float(eta), float(sigma), float(delta), int(seed),
+                        ctypes.byref(opts) if opts is not None else None)
+    _check(st, "hd_init")
+    return h
+
+
+def hd_batch_init(N, eta, sigma, delta, seed, opts: hd_opts | None = None):
+    N = np.ascontiguousarray(N, np.int64)
+    eta = np.ascontiguousarray(eta, np.float64)
+    delta = np.ascontiguousarray(delta, np.float64)
+    seed = np.ascontiguousarray(seed, np.uint64)
+    R = len(N)
+    if not (len(eta) == len(delta) == len(seed) == R):
+        raise ValueError("per-replica arrays must have equal length")
+    h = ctypes.c_void_p()
+    st = load().hd_batch_init(ctypes.byref(h), R, _ptr(N), _ptr(eta), float(sigma), _ptr(delta), _ptr(seed),
+                              ctypes.byref(opts) if opts is not None else None)
+    _check(st, "hd_batch_init")
+    return h
+
+
+def hd_destroy(h):
+    _check(load().hd_destroy(h), "hd_destroy")
+
+
+def hd_set_stream(h, stream_ptr: int | None):
+    _check(load().hd_set_stream(h, ctypes.c_void_p(stream_ptr or 0)), "hd_set_stream")
+
+
+def hd_sweep(h, n: int):
+    _check(load().hd_sweep(h, int(n)), "hd_sweep")
+
+
+def hd_replicas(h) -> int:
+    return int(load().hd_replicas(h))
+
+
+def hd_get_geometry(h, r: int = 0) -> dict:
+    g = hd_geometry()
+    _check(load().hd_get_geometry(h, int(r), ctypes.byref(g)), "hd_get_geometry")
+    return {name: getattr(g, name) for name, _ in hd_geometry._fields_}
+
+
+def _ntot(h) -> int:
+    return sum(hd_get_geometry(h, r)["N"] for r in range(hd_replicas(h)))
+
+
+def hd_pressure(h, want_hist: bool = True):
+    R = hd_replicas(h)
+    bp = np.zeros(R, np.float64)
+    g0 = np.zeros(R, np.float64)
+    K = hd_get_geometry(h, 0)["hist_bins"]
+    hist = np.zeros((R, K), np.uint64) if want_hist else None
+    _check(load().hd_pressure(h, _ptr(bp), _ptr(g0), _ptr(hist)), "hd_pressure")
+    return bp, g0, hist
+
+
+def hd_psi6(h, want_local: bool = True):
+    R = hd_replicas(h)
+    re = np.zeros(R, np.float64)
+    im = np.zeros(R, np.float64)
+    loc = np.zeros((_ntot(h), 2), np.float64) if want_local else None
+    _check(load().hd_psi6(h, _ptr(re), _ptr(im), _ptr(loc)), "hd_psi6")
+    return re + 1j * im, (None if loc is None else loc[:, 0] + 1j * loc[:, 1])
+
+
+def hd_positions(h) -> np.ndarray:
+    out = np.empty((_ntot(h), 2), np.float64)
+    _check(load().hd_positions(h, _ptr(out)), "hd_positions")
+    return out
+
+
+def hd_positions_device(h, dev_ptr: int):
+    _check(load().hd_positions_device(h, ctypes.c_void_p(dev_ptr)), "hd_positions_device")
+
+
+def hd_set_positions(h, xy):
+    a = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+    if a.shape[0] != _ntot(h):
+        raise ValueError("positions must have one row per disk")
+    _check(load().hd_set_positions(h, _ptr(a)), "hd_set_positions")
+
+
+def hd_stats(h):
+    R = hd_replicas(h)
+    a = np.zeros(R, np.uint64)
+    b = np.zeros(R, np.uint64)
+    _check(load().hd_stats(h, _ptr(a), _ptr(b)), "hd_stats")
+    return a, b
+
+
+KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions"]
+
+
+def hd_profile(h, enable: bool):
+    _check(load().hd_profile(h, int(bool(enable))), "hd_profile")
+
+
+def hd_kernel_times(h):
+    """{class: (total device ms or 0 when not profiled, launches)}."""
+    ms = np.zeros(len(KERNEL_CLASSES), np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), np.int64)
+    _check(load().hd_kernel_times(h, _ptr(ms), _ptr(n)), "hd_kernel_times")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+class HardDisks:
+    """Convenience owner of one context (R >= 1 replicas)."""
+
+    def __init__(self, N, eta, delta, seed, sigma=1.0, precision="fp64", lattice="square", trials_per_cell=0,
+                 hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128):
+        opts = make_opts(precision, lattice, trials_per_cell, hist_bins, hist_dr, cell_min, block_threads)
+        if np.ndim(N) == 0:
+            self.h = hd_init(N, eta, sigma, delta, seed, opts)
+        else:
+            self.h = hd_batch_init(N, eta, sigma, delta, seed, opts)
+        self.R = hd_replicas(self.h)
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            hd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        hd_sweep(self.h, n)
+
+    def positions(self):
+        return hd_positions(self.h)
+
+    def set_positions(self, xy):
+        hd_set_positions(self.h, xy)
+
+    def stats(self):
+        return hd_stats(self.h)
+
+    def pressure(self, want_hist=True):
+        return hd_pressure(self.h, want_hist)
+
+    def psi6(self, want_local=True):
+        return hd_psi6(self.h, want_local)
+
+    def geometry(self, r=0):
+        return hd_get_geometry(self.h, r)
+
+    def set_stream(self, stream_ptr):
+        hd_set_stream(self.h, stream_ptr)
+
+    def profile(self, enable=True):
+        hd_profile(self.h, enable)
+
+    def kernel_times(self):
+        return hd_kernel_times(self.h)

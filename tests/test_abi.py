@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: the library builds, loads and exports every entry
+point that include/hd.h declares; argument validation happens on the host;
+without a device the product path fails loudly instead of falling back."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hd.h")
+
+
+@pytest.fixture(scope="module")
+def hdlib():
+    import paper_1211_1645_gb300 as hd
+    return hd, hd.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_paper_calls():
+    syms = declared_symbols()
+    for name in ("hd_init", "hd_sweep", "hd_pressure", "hd_psi6", "hd_positions"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(hdlib):
+    hd, lib = hdlib
+    out = subprocess.run(["nm", "-D", "--defined-only", hd.build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert hasattr(lib, s)
+
+
+def test_status_strings_and_defaults(hdlib):
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    assert b.status_string(0) == "ok"
+    assert "argument" in b.status_string(1)
+    o = b.hd_default_opts()
+    assert (o.precision, o.lattice, o.hist_bins, o.hist_dr, o.cell_min) == (0, 0, 50, 1e-3, 2.0)
+
+
+@pytest.mark.parametrize("N,eta,sigma,delta,kw", [
+    (1, 0.7, 1.0, 0.1, {}),                       # fewer than two disks
+    (256, 0.0, 1.0, 0.1, {}),                     # eta <= 0
+    (256, 0.79, 1.0, 0.1, {}),                    # square lattice would overlap
+    (256, 0.7, 1.0, -0.1, {}),                    # negative step
+    (256, 0.7, 1.0, 3.0, {}),                     # step beyond the cell side
+    (9, 0.7, 1.0, 0.1, {}),                       # fewer than 4 cells per side
+    (256, 0.7, 1.0, 0.1, {"cell_min": 1.5}),      # cells narrower than a diameter
+    (256, 0.7, 1.0, 0.1, {"hist_bins": 10000}),   # too many bins for the fit
+    (256, 0.7, 1.0, 0.1, {"block_threads": 100}),  # not a warp multiple
+])
+def test_invalid_arguments_rejected_on_host(hdlib, N, eta, sigma, delta, kw):
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    opts = b.make_opts(**kw)
+    h = ctypes.c_void_p()
+    st = lib.hd_init(ctypes.byref(h), N, eta, sigma, delta, 1, ctypes.byref(opts))
+    assert st == b.HD_ERR_ARG
+    assert not h.value
+
+
+def test_null_context_calls(hdlib):
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    assert lib.hd_sweep(None, 1) == b.HD_ERR_ARG
+    assert lib.hd_positions(None, None) == b.HD_ERR_ARG
+    assert lib.hd_destroy(None) == b.HD_OK
+    assert lib.hd_replicas(None) == 0
+
+
+def test_no_cpu_fallback_without_gpu(hdlib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    with pytest.raises(b.HDError) as e:
+        b.hd_init(256, 0.7, 1.0, 0.1, 1)
+    assert e.value.status == b.HD_ERR_CUDA

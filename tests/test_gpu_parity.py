@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bar: positions, trial counts and histogram counts bit-exact (FP64 with no FMA
+on both sides, and the fixed-point form); pressure and psi_6 within 1e-12
+relative (FP64), psi_6 of the fixed form (float arithmetic, identical
+operation order) within 2 float ulps of unit magnitude.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PSI_TOL = {"fp64": 1e-12, "fixed": 2.5e-7}
+
+CASES = {
+    "config1_N256": dict(N=256, eta=0.70, delta=0.1, seed=1),
+    "ragged_N1000": dict(N=1000, eta=0.55, delta=0.25, seed=7),
+    "triangular": dict(N=256, eta=0.72, delta=0.15, seed=3, lattice="triangular"),
+    "three_trials": dict(N=400, eta=0.60, delta=0.2, seed=5, nt=3),
+    "cap9_cells": dict(N=300, eta=0.50, delta=0.4, seed=9, cell_min=3.0),
+    "two_disks": dict(N=2, eta=2 * math.pi / 100, delta=1.0, seed=4),
+}
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1211_1645_gb300 as hd
+    hd.load()
+    return hd
+
+
+def make_pair(hd, oracle_mod, form, N, eta, delta, seed, lattice="square", nt=0, cell_min=2.0, K=50, dr=1e-3):
+    g = hd.HardDisks(N, eta, delta, seed, precision=form, lattice=lattice, trials_per_cell=nt, cell_min=cell_min,
+                     hist_bins=K, hist_dr=dr)
+    o = oracle_mod.OracleChain(N, eta, delta, seed, form=form, lattice=lattice, nt=nt, cell_min=cell_min)
+    return g, o
+
+
+def assert_same_state(g, o):
+    att, acc = g.stats()
+    assert (int(att[0]), int(acc[0])) == o.stats()
+    assert np.array_equal(g.positions(), o.positions())
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_chain_bit_exact(hd, oracle_mod, form, case):
+    g, o = make_pair(hd, oracle_mod, form, **CASES[case])
+    geo, ogeo = g.geometry(), o.geometry()
+    assert geo["m"] == ogeo["m"] and geo["L"] == ogeo["L"] and geo["trials_per_cell"] == ogeo["nt"]
+    assert_same_state(g, o)  # the initial lattice
+    for n in (1, 9, 90):
+        g.sweep(n)
+        o.sweep(n)
+        assert_same_state(g, o)
+    g.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_chunk_boundary(hd, oracle_mod, form):
+    """More sweeps in one call than one draw table holds (256)."""
+    g, o = make_pair(hd, oracle_mod, form, 256, 0.70, 0.1, 21)
+    g.sweep(300)
+    o.sweep(300)
+    assert_same_state(g, o)
+    g.sweep(0)
+    assert_same_state(g, o)
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+@pytest.mark.parametrize("K,dr", [(50, 1e-3), (100, 1e-3), (37, 0.004)])
+def test_pressure(hd, oracle_mod, form, K, dr):
+    g, o = make_pair(hd, oracle_mod, form, 1000, 0.70, 0.1, 17, K=K, dr=dr)
+    for n in (0, 25):
+        g.sweep(n)
+        o.sweep(n)
+        bp, g0, hist = g.pressure()
+        want_hist = o.histogram(K, dr)
+        assert np.array_equal(hist[0], want_hist)
+        want = oracle_mod.contact_pressure(want_hist, 1000, o.geometry()["L"], o.realised_dr(dr))
+        assert abs(bp[0] - want["betaP_over_rho"]) <= 1e-12 * abs(want["betaP_over_rho"])
+        assert abs(g0[0] - want["g0"]) <= 1e-12 * max(1.0, abs(want["g0"]))
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+@pytest.mark.parametrize("case", ["config1_N256", "ragged_N1000", "cap9_cells"])
+def test_psi6(hd, oracle_mod, form, case):
+    g, o = make_pair(hd, oracle_mod, form, **CASES[case])
+    g.sweep(40)
+    o.sweep(40)
+    glob, loc = g.psi6()
+    rloc, rglob = o.psi6()
+    assert np.abs(loc - rloc).max() <= PSI_TOL[form]
+    assert abs(glob[0] - rglob) <= 1e-12
+    glob2, none = g.psi6(want_local=False)
+    assert none is None and glob2[0] == glob[0]
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_psi6_low_density_ring_search(hd, oracle_mod, form):
+    """At eta = 0.15 the sixth neighbour often lies beyond the first 5 x 5 cells."""
+    g, o = make_pair(hd, oracle_mod, form, 256, 0.15, 1.0, 8)
+    g.sweep(50)
+    o.sweep(50)
+    glob, loc = g.psi6()
+    rloc, rglob = o.psi6()
+    assert np.abs(loc - rloc).max() <= PSI_TOL[form]
+    assert abs(glob[0] - rglob) <= 1e-12
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_set_positions_roundtrip(hd, oracle_mod, form):
+    g, o = make_pair(hd, oracle_mod, form, 400, 0.65, 0.15, 2)
+    rng = np.random.default_rng(0)
+    o.sweep(30)
+    xy = o.positions() + rng.integers(-2, 3, size=(400, 2)) * o.geometry()["L"]  # periodic images
+    g.set_positions(xy)
+    o.set_positions(xy)
+    assert np.array_equal(g.positions(), o.positions())
+    g.sweep(7)
+    o.sweep(7)
+    assert np.array_equal(g.positions(), o.positions())
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_batched_replicas(hd, oracle_mod, form):
+    """Independent chains of uneven N and eta in one context (the
+    equation-of-state scan as one batch): each equals its own oracle chain."""
+    Ns = [16 ** 2, 24 ** 2, 32 ** 2, 20 ** 2, 17 ** 2]
+    etas = [0.700, 0.701, 0.702, 0.703, 0.704]
+    deltas = [0.1, 0.12, 0.09, 0.11, 0.1]
+    seeds = [101, 102, 103, 104, 105]
+    g = hd.HardDisks(Ns, etas, deltas, seeds, precision=form)
+    os_ = [oracle_mod.OracleChain(n, e, d, s, form=form) for n, e, d, s in zip(Ns, etas, deltas, seeds)]
+    g.sweep(60)
+    for o in os_:
+        o.sweep(60)
+    att, acc = g.stats()
+    xy = g.positions()
+    off = 0
+    bp, g0, hist = g.pressure()
+    glob, loc = g.psi6()
+    for r, o in enumerate(os_):
+        assert (int(att[r]), int(acc[r])) == o.stats()
+        assert np.array_equal(xy[off:off + Ns[r]], o.positions())
+        h = o.histogram(50, 1e-3)
+        assert np.array_equal(hist[r], h)
+        want = oracle_mod.contact_pressure(h, Ns[r], o.geometry()["L"], o.realised_dr(1e-3))
+        assert abs(bp[r] - want["betaP_over_rho"]) <= 1e-12 * want["betaP_over_rho"]
+        rloc, rglob = o.psi6()
+        assert np.abs(loc[off:off + Ns[r]] - rloc).max() <= PSI_TOL[form]
+        assert abs(glob[r] - rglob) <= 1e-12
+        off += Ns[r]
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_full_size_config2(hd, oracle_mod, form):
+    """N = 256^2 at eta = 0.708 (liquid side), whole state compared."""
+    g, o = make_pair(hd, oracle_mod, form, 65536, 0.708, 0.1, 2)
+    g.sweep(20)
+    o.sweep(20)
+    assert_same_state(g, o)
+    bp, _, hist = g.pressure()
+    assert np.array_equal(hist[0], o.histogram(50, 1e-3))
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_full_size_config3(hd, oracle_mod, form):
+    """N = 1024^2 at eta = 0.716 (coexistence), the benchmark workload: whole
+    state, histogram and every psi_j compared after three sweeps."""
+    N = 1024 * 1024
+    g, o = make_pair(hd, oracle_mod, form, N, 0.716, 0.1, 1)
+    g.sweep(3)
+    o.sweep(3)
+    assert_same_state(g, o)
+    bp, _, hist = g.pressure()
+    want_hist = o.histogram(50, 1e-3)
+    assert np.array_equal(hist[0], want_hist)
+    want = oracle_mod.contact_pressure(want_hist, N, o.geometry()["L"], o.realised_dr(1e-3))
+    assert abs(bp[0] - want["betaP_over_rho"]) <= 1e-12 * want["betaP_over_rho"]
+    glob, loc = g.psi6()
+    rloc, rglob = o.psi6()
+    assert np.abs(loc - rloc).max() <= PSI_TOL[form]
+    assert abs(glob[0] - rglob) <= 1e-12
+
+
+def test_full_size_config5(hd, oracle_mod):
+    """N = 2048^2 at eta = 0.720 from the shifted-row lattice, fixed point."""
+    N = 2048 * 2048
+    g, o = make_pair(hd, oracle_mod, "fixed", N, 0.720, 0.1, 5, lattice="triangular")
+    g.sweep(2)
+    o.sweep(2)
+    assert_same_state(g, o)
+    _, _, hist = g.pressure()
+    assert np.array_equal(hist[0], o.histogram(50, 1e-3))
+
+
+def test_reach_error_is_reported_and_recoverable(hd, oracle_mod):
+    from paper_1211_1645_gb300.hd import HD_ERR_REACH, HDError
+    g = hd.HardDisks(2, 2 * math.pi / 100, 1.0, 4, hist_bins=500, hist_dr=0.01)
+    with pytest.raises(HDError) as e:
+        g.pressure()
+    assert e.value.status == HD_ERR_REACH
+    g.sweep(5)  # still usable
+    assert g.stats()[0][0] > 0
+
+
+def test_psi6_reach_error(hd):
+    from paper_1211_1645_gb300.hd import HD_ERR_REACH, HDError
+    N, L = 8, 40.0
+    g = hd.HardDisks(N, N * math.pi / L ** 2, 0.1, 1)
+    # rows 10 apart in x and 20 in y: the sixth neighbour (22.4 sigma) lies beyond
+    # the widest stencil a 40-sigma box allows (9 rings of 2-sigma cells)
+    xy = np.array([[5 + 10 * (k % 4), 5 + 20 * (k // 4)] for k in range(N)], dtype=np.float64)
+    g.set_positions(xy)
+    with pytest.raises(HDError) as e:
+        g.psi6()
+    assert e.value.status == HD_ERR_REACH
+    g.sweep(1)
+
+
+def test_overflow_rejected_on_set_positions(hd):
+    from paper_1211_1645_gb300.hd import HD_ERR_OVERFLOW, HDError
+    g = hd.HardDisks(256, 0.7, 0.1, 1)
+    xy = g.positions()
+    xy[:5] = [[1.0, 1.0], [1.1, 1.0], [1.2, 1.0], [1.3, 1.0], [1.4, 1.0]]  # five disks in one cell
+    with pytest.raises(HDError) as e:
+        g.set_positions(xy)
+    assert e.value.status == HD_ERR_OVERFLOW
