@@ -62,9 +62,14 @@ typedef struct hd_opts {
     int32_t hist_bins;       /* K, contact-histogram bins [50]                      */
     double hist_dr;          /* bin width in sigma [1e-3]; Sec. II.C.1              */
     double cell_min;         /* minimum cell side in sigma, >= 2 [2]; Sec. II.B     */
-    int32_t block_threads;   /* threads per block of the sweep kernels [128]        */
-    int32_t reserved;
+    int32_t block_threads;   /* threads per block of the split sweep kernels [128]  */
+    int32_t sweep_kernel;    /* HD_SWEEP_SPLIT: a rebuild launch and four colour-pass
+                                launches per sweep [default]; HD_SWEEP_FUSED: one
+                                launch per sweep, tiles staged in shared memory.
+                                Both give bit-identical chains.                     */
 } hd_opts;
+
+enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1 };
 
 /* Geometry of one replica as realised by the library. */
 typedef struct hd_geometry {
@@ -198,7 +203,8 @@ typedef enum hd_kernel_class {
     HD_K_PSI6 = 5,       /* local psi_6                                       */
     HD_K_PSI6_REDUCE = 6,/* global Psi_6 reduction                            */
     HD_K_POSITIONS = 7,  /* cell frame to global positions                    */
-    HD_KERNEL_CLASSES = 8
+    HD_K_SWEEP = 8,      /* one fused sweep (rebuild and four passes)         */
+    HD_KERNEL_CLASSES = 9
 } hd_kernel_class;
 
 hd_status hd_profile(hd_ctx *ctx, int32_t enable);

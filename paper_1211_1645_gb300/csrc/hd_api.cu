@@ -37,11 +37,13 @@ struct hd_ctx {
     int K = 50;
     int lattice = 0;
     int threads = 128;
+    bool fused = false;
+    int tile = 48;
     double sigma = 1.0;
     std::vector<Rep> reps;
     std::vector<int64_t> nlat;
     int64_t Ntot = 0, Ctot = 0;
-    int blocks_cell = 0, blocks_act = 0;
+    int blocks_cell = 0, blocks_act = 0, blocks_tile = 0;
     Rep* reps_d = nullptr;
     CellBufs buf[2] = {};
     int cur = 0;
@@ -79,6 +81,7 @@ struct hd_ctx {
         c.threads = threads;
         c.blocks_cell = blocks_cell;
         c.blocks_act = blocks_act;
+        c.blocks_tile = blocks_tile;
         c.stream = stream;
         return c;
     }
@@ -145,6 +148,7 @@ hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64
     r.w = w;
     r.w_below = std::nextafter(w, 0.0);
     r.L = L;
+    r.Lm = fixed ? double(r.LF) / kFx : L;
     r.delta = dhat;
     r.sigma = sigma;
     r.key0 = uint32_t(seed & 0xffffffffu);
@@ -198,10 +202,10 @@ bool bin_disk(const hd_ctx* ctx, const Rep& rep, HostCells& h, int64_t id, doubl
         bin_fp64(x, rep, cx, ux);
         bin_fp64(y, rep, cy, uy);
     }
-    const int64_t cell = rep.cell_off + int64_t(cy) * rep.m + cx;
+    const int64_t cell = hd::cell_index(rep, cx, cy);
     const int k = h.cnt[cell];
     if (k >= ctx->cap) return false;
-    const int64_t slot = cell * ctx->cap + k;
+    const int64_t slot = int64_t(k) * ctx->Ctot + cell;
     if (ctx->fixed) {
         h.posfx[2 * slot] = fx;
         h.posfx[2 * slot + 1] = fy;
@@ -309,6 +313,7 @@ void hd_default_opts(hd_opts* o) {
     o->hist_dr = 1e-3;
     o->cell_min = 2.0;
     o->block_threads = 128;
+    o->sweep_kernel = HD_SWEEP_SPLIT;
 }
 
 const char* hd_status_string(hd_status s) {
@@ -339,11 +344,13 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         if (opts_in->hist_dr > 0.0) o.hist_dr = opts_in->hist_dr;
         if (opts_in->cell_min > 0.0) o.cell_min = opts_in->cell_min;
         if (opts_in->block_threads > 0) o.block_threads = opts_in->block_threads;
+        o.sweep_kernel = opts_in->sweep_kernel;
     }
     if (o.precision != HD_FP64 && o.precision != HD_FIXED32) return HD_ERR_ARG;
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
     if (!(o.cell_min >= 2.0) || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
     if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
+    if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT) return HD_ERR_ARG;
 
     std::vector<Plan> plans(static_cast<size_t>(R));
     int cap = 4;
@@ -362,6 +369,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->K = o.hist_bins;
     ctx->lattice = o.lattice;
     ctx->threads = o.block_threads;
+    ctx->fused = o.sweep_kernel == HD_SWEEP_FUSED;
+    ctx->tile = hd::fused_tile(ctx->fixed, cap);
     ctx->sigma = sigma;
     ctx->sweeps.assign(size_t(R), 0);
     const int64_t DR = std::llround(o.hist_dr * kFx);
@@ -370,13 +379,16 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         return HD_ERR_ARG;
     }
     int64_t cell_off = 0, id_off = 0;
-    int blk_cell = 0, blk_act = 0;
+    int blk_cell = 0, blk_act = 0, blk_tile = 0;
     for (int r = 0; r < R; ++r) {
         Rep rep = plans[size_t(r)].rep;
         rep.cell_off = cell_off;
         rep.id_off = id_off;
         rep.blk_cell = blk_cell;
         rep.blk_act = blk_act;
+        rep.blk_tile = blk_tile;
+        const int64_t tx = (rep.m + ctx->tile - 1) / ctx->tile;
+        blk_tile += int(tx * tx);
         const int64_t ncell = int64_t(rep.m) * rep.m;
         const int64_t nact = int64_t(rep.hm) * rep.hm;
         cell_off += ncell;
@@ -395,13 +407,25 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     }
     ctx->Ctot = cell_off;
     ctx->Ntot = id_off;
+    if (ctx->Ctot * int64_t(cap) >= (int64_t(1) << 31)) {
+        delete ctx;
+        return HD_ERR_ARG;  // cell and slot indices are 32-bit in the kernels
+    }
+    for (Rep& rep : ctx->reps) {
+        rep.stride = ctx->Ctot;
+        rep.coff = uint32_t(rep.cell_off);
+        rep.stride32 = uint32_t(ctx->Ctot);
+        rep.hh = rep.hm * rep.hm;
+    }
     ctx->blocks_cell = blk_cell;
     ctx->blocks_act = blk_act;
+    ctx->blocks_tile = blk_tile;
 
     const size_t slots = size_t(ctx->Ctot) * cap;
     bool ok = dev_alloc(ctx, &ctx->reps_d, size_t(R));
     for (int b = 0; b < 2 && ok; ++b) {
-        ok = ok && dev_alloc(ctx, &ctx->buf[b].cnt, size_t(ctx->Ctot));
+        // occupancy bytes are claimed with 32-bit atomics: pad to whole words
+        ok = ok && dev_alloc(ctx, &ctx->buf[b].cnt, size_t(ctx->Ctot) + 4);
         ok = ok && dev_alloc(ctx, &ctx->buf[b].pid, slots);
         if (ctx->fixed) {
             int2* p = nullptr;
@@ -445,7 +469,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     cu = cu && cudaMemset(ctx->sweep_ctr, 0, sizeof(uint64_t) * size_t(R)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * size_t(2 * R)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
-    cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot)) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->buf[0].cnt, 0, size_t(ctx->Ctot) + 4) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot) + 4) == cudaSuccess;
     if (!cu) {
         free_ctx(ctx);
         return HD_ERR_CUDA;
@@ -512,7 +537,14 @@ hd_status hd_sweep(hd_ctx* ctx, int64_t n) {
     while (left > 0) {
         const int nc = int(std::min<int64_t>(left, hd::kMaxChunk));
         HD_CK(ctx, launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); }));
-        for (int j = 1; j <= nc; ++j) {
+        for (int j = 1; j <= nc && ctx->fused; ++j) {
+            HD_CK(ctx, launch(ctx, HD_K_SWEEP, [&] {
+                return hd::launch_sweep_fused(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1],
+                                              ctx->counters, ctx->err);
+            }));
+            ctx->cur ^= 1;
+        }
+        for (int j = 1; j <= nc && !ctx->fused; ++j) {
             HD_CK(ctx, launch(ctx, HD_K_REBUILD, [&] {
                 return hd::launch_rebuild(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->err);
             }));

@@ -1,0 +1,330 @@
+// hd_cell.cuh -- per-cell steps of the checkerboard sweep (Engel et al.,
+// arXiv:1211.1645, Sec. II.B), shared by the split kernels (one launch per
+// rebuild and per colour pass) and the fused kernel (one launch per sweep):
+//   gather_cell  builds one cell of the new shifted frame from the 2 x 2 old
+//                cells that can feed it, occupants ordered by ascending id;
+//   try_cell     shuffles one active cell's occupants and makes its serial
+//                trial moves against the cell itself and its neighbours.
+#pragma once
+
+#include <climits>
+#include <type_traits>
+
+#include "hd_device.cuh"
+
+namespace hd {
+
+template <bool FIX>
+using P2 = std::conditional_t<FIX, int2, double2>;
+
+// Slots 0 and 1 are loaded unconditionally (together they hold nearly every
+// disk at liquid densities); higher slots only when the cell is that full.
+constexpr int kEagerSlots = 2;
+
+// One cell as loaded by a thread: occupancy and the first kEagerSlots slots
+// in registers; a higher slot is fetched when a (rare) crowded cell needs it.
+template <bool FIX, bool IDS>
+struct CellRegs {
+    const P2<FIX>* pos;   // slot 0 of this cell; slot k at pos[k * stride]
+    const int32_t* pid;
+    P2<FIX> s[kEagerSlots];
+    int32_t id[IDS ? kEagerSlots : 1];
+    int n;
+
+    __device__ __forceinline__ P2<FIX> slot(int k, uint32_t stride) const {
+        if (k == 0) return s[0];
+        if (k == 1) return s[1];
+        return __ldg(pos + size_t(k) * stride);
+    }
+    __device__ __forceinline__ int32_t slot_id(int k, uint32_t stride) const {
+        if constexpr (IDS) {
+            if (k == 0) return id[0];
+            if (k == 1) return id[1];
+            return __ldg(pid + size_t(k) * stride);
+        }
+        return 0;
+    }
+};
+
+// Occupancy of a cell, clamped to its capacity (a count above capacity only
+// arises after an overflow, which the kernels report through the error flag).
+template <int CAP>
+__device__ __forceinline__ int occupancy(const uint8_t* __restrict__ cnt, uint32_t c) {
+    const int n = __ldg(cnt + c);
+    return n < CAP ? n : CAP;
+}
+
+template <bool FIX, bool IDS, int CAP = 4>
+__device__ __forceinline__ void load_cell(const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
+                                          const int32_t* __restrict__ pid, uint32_t stride, uint32_t c,
+                                          CellRegs<FIX, IDS>& out) {
+    out.n = occupancy<CAP>(cnt, c);
+    out.pos = pos + c;
+    out.pid = IDS ? pid + c : nullptr;
+#pragma unroll
+    for (int k = 0; k < kEagerSlots; ++k) {
+        out.s[k] = __ldg(pos + size_t(k) * stride + c);
+        if constexpr (IDS) out.id[k] = __ldg(pid + size_t(k) * stride + c);
+    }
+}
+
+// Shift difference between two frames (old minus new) and the direction of
+// the second feeding cell per axis (-1: old c-1 also feeds c; +1: old c+1).
+template <bool FIX>
+struct ShiftDelta {
+    double dx, dy;
+    int32_t fx, fy;
+    int ox, oy;
+
+    __device__ __forceinline__ ShiftDelta(const Frame& fo, const Frame& fn) {
+        if constexpr (FIX) {
+            dx = dy = 0.0;
+            fx = fo.Sx - fn.Sx;
+            fy = fo.Sy - fn.Sy;
+            ox = fx >= 0 ? -1 : 1;
+            oy = fy >= 0 ? -1 : 1;
+        } else {
+            fx = fy = 0;
+            dx = __dsub_rn(fo.sx, fn.sx);
+            dy = __dsub_rn(fo.sy, fn.sy);
+            ox = dx >= 0.0 ? -1 : 1;
+            oy = dy >= 0.0 ? -1 : 1;
+        }
+    }
+};
+
+// The occupants of one new cell, ascending id; id INT_MAX marks an empty slot.
+template <bool FIX, int CAP>
+struct NewCell {
+    int32_t id[CAP];
+    P2<FIX> p[CAP];
+    int n;
+    bool over;
+};
+
+template <bool FIX, int CAP>
+__device__ __forceinline__ void cswap(NewCell<FIX, CAP>& c, int a, int b) {
+    if (c.id[b] < c.id[a]) {
+        const int32_t t = c.id[a];
+        c.id[a] = c.id[b];
+        c.id[b] = t;
+        const P2<FIX> u = c.p[a];
+        c.p[a] = c.p[b];
+        c.p[b] = u;
+    }
+}
+
+// Build new cell (cx, cy) from its four feeding old cells src[b] at (ocx[b],
+// ocy[b]): every occupant is moved into the new frame by the same per-disk
+// frame change (frame_change_fp64 / frame_change_fixed); those that land in
+// (cx, cy) are kept, then ordered by id with a sorting network.
+template <bool FIX, int CAP>
+__device__ __forceinline__ void gather_cell(const Rep& rep, const ShiftDelta<FIX>& sd,
+                                            const CellRegs<FIX, true> (&src)[4], const int (&ocx)[4],
+                                            const int (&ocy)[4], int cx, int cy, NewCell<FIX, CAP>& out) {
+    out.n = 0;
+    out.over = false;
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+        out.id[q] = INT_MAX;
+        out.p[q] = P2<FIX>{};
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int nb = src[b].n;
+        for (int k = 0; k < nb; ++k) {
+            const P2<FIX> q = src[b].slot(k, rep.stride32);
+            int tcx, tcy;
+            P2<FIX> nq;
+            if constexpr (FIX) {
+                frame_change_fixed(sd.fx, rep.W, rep.m, ocx[b], q.x, tcx, nq.x);
+                frame_change_fixed(sd.fy, rep.W, rep.m, ocy[b], q.y, tcy, nq.y);
+            } else {
+                frame_change_fp64(sd.dx, rep.w, rep.w_below, rep.m, ocx[b], q.x, tcx, nq.x);
+                frame_change_fp64(sd.dy, rep.w, rep.w_below, rep.m, ocy[b], q.y, tcy, nq.y);
+            }
+            if (tcx != cx || tcy != cy) continue;
+            const int32_t id = src[b].slot_id(k, rep.stride32);
+            if (out.n >= CAP) {
+                out.over = true;
+                continue;
+            }
+#pragma unroll
+            for (int s = 0; s < CAP; ++s)
+                if (s == out.n) {
+                    out.id[s] = id;
+                    out.p[s] = nq;
+                }
+            ++out.n;
+        }
+    }
+    if (out.n > 1) {
+        if constexpr (CAP == 4) {
+            cswap(out, 0, 1);
+            cswap(out, 2, 3);
+            cswap(out, 0, 2);
+            cswap(out, 1, 3);
+            cswap(out, 1, 2);
+        } else {
+#pragma unroll
+            for (int i = 1; i < CAP; ++i)
+#pragma unroll
+                for (int s = i; s > 0; --s) cswap(out, s - 1, s);
+        }
+    }
+}
+
+// Order the first n occupants of a cell by ascending id, in registers
+// (slots at or beyond n are padded with id INT_MAX so they stay last).
+template <bool FIX, int CAP>
+__device__ __forceinline__ void sort_by_id(P2<FIX> (&P)[CAP], int32_t (&id)[CAP], int n) {
+    NewCell<FIX, CAP> c;
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+        c.p[q] = P[q];
+        c.id[q] = q < n ? id[q] : INT_MAX;
+    }
+    if constexpr (CAP == 4) {
+        cswap(c, 0, 1);
+        cswap(c, 2, 3);
+        cswap(c, 0, 2);
+        cswap(c, 1, 3);
+        cswap(c, 1, 2);
+    } else {
+#pragma unroll
+        for (int i = 1; i < CAP; ++i)
+#pragma unroll
+            for (int s = i; s > 0; --s) cswap(c, s - 1, s);
+    }
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+        P[q] = c.p[q];
+        id[q] = c.id[q];
+    }
+}
+
+// Claim the next free slot of cell di by adding one to its occupancy byte;
+// returns the slot.  The byte counters of four consecutive cells share one
+// 32-bit word (the counter array is 4-byte aligned and padded).
+__device__ __forceinline__ int claim_slot(uint8_t* cnt, uint32_t di) {
+    unsigned int* word = reinterpret_cast<unsigned int*>(cnt) + (di >> 2);
+    const unsigned int shift = 8u * (di & 3u);
+    const unsigned int old = atomicAdd(word, 1u << shift);
+    return int((old >> shift) & 0xFFu);
+}
+
+__device__ __forceinline__ uint32_t pick_word(const uint4& w0, const uint4& w1, int i) {
+    switch (i) {
+        case 0: return w0.x;
+        case 1: return w0.y;
+        case 2: return w0.z;
+        case 3: return w0.w;
+        case 4: return w1.x;
+        case 5: return w1.y;
+        case 6: return w1.z;
+        default: return w1.w;
+    }
+}
+
+// Overlap test of a proposed position np against one occupant q whose cell is
+// (ox, oy) cells away from the moving disk's cell: true when clear (the centre
+// distance is at least 2 sigma).
+template <bool FIX>
+__device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, const P2<FIX>& np, const Rep& rep) {
+    if constexpr (FIX) {
+        const int32_t rx = (q.x + ox * rep.W) - np.x;
+        const int32_t ry = (q.y + oy * rep.W) - np.y;
+        return (int64_t(rx) * rx + int64_t(ry) * ry) >= kFxDiam2;
+    } else {
+        const double offx = ox < 0 ? -rep.w : (ox > 0 ? rep.w : 0.0);
+        const double offy = oy < 0 ? -rep.w : (oy > 0 ? rep.w : 0.0);
+        const double rx = __dsub_rn(__dadd_rn(q.x, offx), np.x);
+        const double ry = __dsub_rn(__dadd_rn(q.y, offy), np.y);
+        return !(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) < 4.0);
+    }
+}
+
+// One active cell with n >= 1 occupants P[0..n) (ascending id): Fisher-Yates
+// shuffle with one 32-bit word per swap, then rep.nt serial trials; trial t
+// moves the occupant at position t mod n of the shuffled order by a step
+// uniform in [-delta, delta]^2, rejected if it leaves the cell or comes
+// closer than 2 sigma to another occupant or to a disk of the eight
+// neighbouring cells (`neighbours_clear(np)`).  Updates P; returns accepts.
+template <bool FIX, int CAP, class NbrClear>
+__device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
+                                             NbrClear&& neighbours_clear) {
+    uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
+    if (n > 1) {
+        uint4 w0 = philox(sweep, 0u, cl, kTagShuffle, rep.key0, rep.key1), w1 = make_uint4(0, 0, 0, 0);
+        if (CAP > 5 && n > 5) w1 = philox(sweep, 1u, cl, kTagShuffle, rep.key0, rep.key1);
+#pragma unroll
+        for (int k = CAP - 1; k >= 1; --k) {
+            if (k < n) {
+                const uint32_t jj = bounded(pick_word(w0, w1, n - 1 - k), uint32_t(k + 1));
+                const uint64_t vk = (order >> (4 * k)) & 0xFull;
+                const uint64_t vj = (order >> (4 * jj)) & 0xFull;
+                order &= ~((0xFull << (4 * k)) | (0xFull << (4 * jj)));
+                order |= (vj << (4 * k)) | (vk << (4 * jj));
+            }
+        }
+    }
+    uint32_t acc = 0;
+    for (int t = 0; t < rep.nt; ++t) {
+        const uint4 u = philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
+        const int slot = int((order >> (4 * (n == 1 ? 0 : t % n))) & 0xFull);
+        P2<FIX> me = P[0];
+#pragma unroll
+        for (int q = 1; q < CAP; ++q)
+            if (q == slot) me = P[q];
+        P2<FIX> np;
+        bool ok;
+        if constexpr (FIX) {
+            const uint32_t span = uint32_t(2 * rep.D + 1);
+            np.x = me.x + (int32_t(bounded(u.x, span)) - rep.D);
+            np.y = me.y + (int32_t(bounded(u.y, span)) - rep.D);
+            ok = np.x >= 0 && np.x < rep.W && np.y >= 0 && np.y < rep.W;
+        } else {
+            np.x = __dadd_rn(me.x, step_fp64(u.x, u.y, rep.delta));
+            np.y = __dadd_rn(me.y, step_fp64(u.z, u.w, rep.delta));
+            ok = np.x >= 0.0 && np.x < rep.w && np.y >= 0.0 && np.y < rep.w;
+        }
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < CAP; ++q)
+                if (q < n && q != slot) ok = ok && pair_clear<FIX>(P[q], 0, 0, np, rep);
+            ok = ok && neighbours_clear(np);
+        }
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < CAP; ++q)
+                if (q == slot) P[q] = np;
+            ++acc;
+        }
+    }
+    return acc;
+}
+
+// Sum two per-thread counters over the block and add them to counters[2r],
+// counters[2r + 1] with one atomic each.  Every thread of the block must call.
+__device__ __forceinline__ void block_count(uint32_t att, uint32_t acc, unsigned long long* counters, int r) {
+    __shared__ unsigned int s_att[32], s_acc[32];
+    att = __reduce_add_sync(0xffffffffu, att);
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_att[warp] = att;
+        s_acc[warp] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ta = 0, tc = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+            ta += s_att[w];
+            tc += s_acc[w];
+        }
+        if (ta) atomicAdd(&counters[2 * r], ta);
+        if (tc) atomicAdd(&counters[2 * r + 1], tc);
+    }
+}
+
+}  // namespace hd

@@ -22,14 +22,21 @@ struct Rep {
     int64_t cell_off;   // first cell of the replica in the concatenated cell arrays
     int64_t id_off;     // first disk of the replica in the global id order
     int64_t LF;         // fixed point: box side m * W
+    int64_t stride;     // distance between slot planes (cells of all replicas)
+    uint32_t coff;      // cell_off as 32 bits (all cell and slot indices fit in 32 bits)
+    uint32_t stride32;  // stride as 32 bits
+    int32_t hh;         // cells per colour plane, (m/2)^2
     int32_t m, hm;      // cells per side, m / 2
     int32_t nt;         // trial moves per occupied active cell per pass
     int32_t blk_cell;   // first block of the replica in whole-cell grids
     int32_t blk_act;    // first block of the replica in active-cell grids
+    int32_t blk_tile;   // first block of the replica in fused-sweep tile grids
+    int32_t pad_;
     int32_t W, D;       // fixed point: cell side, maximum step (units 2^-24 sigma)
     int32_t hist_R;     // cell reach of the contact histogram
     double w, w_below;  // FP64 cell side and the largest double below it
     double L, delta;    // FP64 box side and maximum step (sigma units)
+    double Lm;          // realised box side (fixed form: m W 2^-24) for g(r) and eta
     double sigma;       // disk radius (output scale)
     double dr;          // realised histogram bin width (sigma units)
     uint32_t key0, key1;
@@ -70,13 +77,44 @@ __device__ __forceinline__ uint32_t bounded(uint32_t word, uint32_t n) { return 
 
 __device__ __forceinline__ int wrap_cell(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
 
+// Cells are stored in four colour planes (parities of cx and cy), each an
+// (m/2) x (m/2) row-major array; slot k of every cell lives in its own plane
+// at distance k * stride.  The cells a warp touches in a colour pass -- its
+// 32 active cells and each of their eight neighbours -- are then consecutive
+// entries of one plane.
+__host__ __device__ __forceinline__ int64_t cell_index(const Rep& r, int cx, int cy) {
+    return r.cell_off + int64_t(((cy & 1) << 1) | (cx & 1)) * r.hm * r.hm + int64_t(cy >> 1) * r.hm + (cx >> 1);
+}
+
+// Inverse of cell_index for a replica-local planar position a in [0, m^2).
+__device__ __forceinline__ void cell_coords(const Rep& r, int64_t a, int& cx, int& cy) {
+    const uint32_t au = uint32_t(a), hh = uint32_t(r.hh), hm = uint32_t(r.hm);
+    const uint32_t plane = au / hh;
+    const uint32_t rem = au - plane * hh;
+    const uint32_t row = rem / hm;
+    cx = 2 * int(rem - row * hm) + int(plane & 1);
+    cy = 2 * int(row) + int(plane >> 1);
+}
+
+// Column part and row part of a 32-bit colour-planar cell index:
+// cell_index = coff + row_part(cy) + col_part(cx).
+__device__ __forceinline__ uint32_t col_part(const Rep& r, int cx) {
+    return uint32_t(cx & 1) * uint32_t(r.hh) + uint32_t(cx >> 1);
+}
+__device__ __forceinline__ uint32_t row_part(const Rep& r, int cy) {
+    return uint32_t(cy & 1) * uint32_t(2 * r.hh) + uint32_t(cy >> 1) * uint32_t(r.hm);
+}
+
+// Grids over all replicas: whole cells, active cells of one colour, tiles.
+enum GridKind { kGridCell = 0, kGridAct = 1, kGridTile = 2 };
+
 // Replica owning block `blk`, given per-replica first blocks (ascending).
-template <bool ACT>
+template <int KIND>
 __device__ __forceinline__ int find_rep(const Rep* __restrict__ reps, int R, int blk) {
     int lo = 0, hi = R - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int start = ACT ? reps[mid].blk_act : reps[mid].blk_cell;
+        const int start = KIND == kGridAct ? reps[mid].blk_act : (KIND == kGridTile ? reps[mid].blk_tile : reps[mid].blk_cell);
         if (start <= blk) lo = mid; else hi = mid - 1;
     }
     return lo;

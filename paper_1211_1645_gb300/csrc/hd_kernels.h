@@ -24,6 +24,7 @@ struct LaunchCfg {
     int threads;       // threads per block
     int blocks_cell;   // whole-cell grid size (all replicas)
     int blocks_act;    // active-cell grid size (all replicas)
+    int blocks_tile;   // fused-sweep tile grid size (all replicas)
     cudaStream_t stream;
 };
 
@@ -32,6 +33,11 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
                            int* err);
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters);
+// One whole sweep (rebuild + four colour passes) per launch, staged in shared
+// memory by tiles of fused_tile(fixed, cap) cells per side.
+int fused_tile(bool fixed, int cap);
+cudaError_t launch_sweep_fused(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,
+                               unsigned long long* counters, int* err);
 cudaError_t launch_positions(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy);
 
 // Measurement.

@@ -31,28 +31,29 @@ k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ ed
     extern __shared__ unsigned int s_bins[];
     for (int b = threadIdx.x; b < K; b += blockDim.x) s_bins[b] = 0u;
     __syncthreads();
-    const int r = find_rep<false>(reps, R, blockIdx.x);
+    const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep& rep = reps[r];
     const int m = rep.m;
-    const int64_t c = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
-    if (c < int64_t(m) * m) {
-        const int cx = int(c % m), cy = int(c / m);
-        const int64_t cell = rep.cell_off + c;
-        const int n = cnt[cell];
+    const int64_t a = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
+    if (a < int64_t(m) * m) {
+        int cx, cy;
+        cell_coords(rep, a, cx, cy);
+        const int64_t cell = rep.cell_off + a;
+        const int n = min(int(cnt[cell]), CAP);
         const int RR = rep.hist_R;
         const double e0 = edges[0], eK = edges[K];
         const long long f0 = edgesF[0], fK = edgesF[K];
         for (int k = 0; k < n; ++k) {
-            const P2<FIX> me = pos[cell * CAP + k];
-            const int32_t idme = pid[cell * CAP + k];
+            const P2<FIX> me = pos[k * rep.stride + cell];
+            const int32_t idme = pid[k * rep.stride + cell];
             for (int dcy = -RR; dcy <= RR; ++dcy) {
                 for (int dcx = -RR; dcx <= RR; ++dcx) {
-                    const int64_t nc = rep.cell_off + int64_t(wrap_cell(cy + dcy, m)) * m + wrap_cell(cx + dcx, m);
-                    const int nn = cnt[nc];
+                    const int64_t nc = cell_index(rep, wrap_cell(cx + dcx, m), wrap_cell(cy + dcy, m));
+                    const int nn = min(int(cnt[nc]), CAP);
                     for (int q = 0; q < nn; ++q) {
-                        const int32_t idq = pid[nc * CAP + q];
+                        const int32_t idq = pid[q * rep.stride + nc];
                         if (idq <= idme) continue;
-                        const P2<FIX> o = pos[nc * CAP + q];
+                        const P2<FIX> o = pos[q * rep.stride + nc];
                         int bin;
                         if constexpr (FIX) {
                             const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
@@ -102,7 +103,7 @@ __global__ void k_fit(const Rep* __restrict__ reps, int K, const unsigned long l
     const int r = blockIdx.x;
     const Rep& rep = reps[r];
     const double PI = 3.14159265358979323846;
-    const double V = __dmul_rn(rep.L, rep.L);
+    const double V = __dmul_rn(rep.Lm, rep.Lm);
     const double p = __dmul_rn(__dmul_rn(double(rep.N), double(rep.N)), 0.5);
     const double dr = rep.dr;
     for (int k = 0; k < K; ++k) {
@@ -197,12 +198,12 @@ __device__ __forceinline__ void scan_cell(const Rep& rep, const uint8_t* __restr
                                           const int32_t* __restrict__ pid, int cx, int cy, int dcx, int dcy,
                                           const P2<FIX>& me, int32_t idme, Nbr<FIX>& nb) {
     const int m = rep.m;
-    const int64_t nc = rep.cell_off + int64_t(wrap_cell(cy + dcy, m)) * m + wrap_cell(cx + dcx, m);
-    const int nn = cnt[nc];
+    const int64_t nc = cell_index(rep, wrap_cell(cx + dcx, m), wrap_cell(cy + dcy, m));
+    const int nn = min(int(cnt[nc]), CAP);
     for (int q = 0; q < nn; ++q) {
-        const int32_t idq = pid[nc * CAP + q];
+        const int32_t idq = pid[q * rep.stride + nc];
         if (idq == idme) continue;
-        const P2<FIX> o = pos[nc * CAP + q];
+        const P2<FIX> o = pos[q * rep.stride + nc];
         if constexpr (FIX) {
             const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
             const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
@@ -220,23 +221,24 @@ __global__ void __launch_bounds__(256)
 k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
        const int32_t* __restrict__ pid, double2* __restrict__ local, double2* __restrict__ partial,
        int* __restrict__ err) {
-    const int r = find_rep<false>(reps, R, blockIdx.x);
+    const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep& rep = reps[r];
     const int m = rep.m;
-    const int64_t c = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
+    const int64_t a = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
     double sr = 0.0, si = 0.0;
-    if (c < int64_t(m) * m) {
-        const int cx = int(c % m), cy = int(c / m);
-        const int64_t cell = rep.cell_off + c;
-        const int n = cnt[cell];
+    if (a < int64_t(m) * m) {
+        int cx, cy;
+        cell_coords(rep, a, cx, cy);
+        const int64_t cell = rep.cell_off + a;
+        const int n = min(int(cnt[cell]), CAP);
         int rmax = (m - 1) / 2;
         if constexpr (FIX) {
             const int lim = int((int64_t(1) << 31) / rep.W) - 1;
             if (lim < rmax) rmax = lim;
         }
         for (int k = 0; k < n; ++k) {
-            const P2<FIX> me = pos[cell * CAP + k];
-            const int32_t idme = pid[cell * CAP + k];
+            const P2<FIX> me = pos[k * rep.stride + cell];
+            const int32_t idme = pid[k * rep.stride + cell];
             Nbr<FIX> nb;
             nb.n = 0;
             bool ok = false;

@@ -37,7 +37,7 @@ class hd_opts(ctypes.Structure):
         ("hist_dr", ctypes.c_double),
         ("cell_min", ctypes.c_double),
         ("block_threads", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("sweep_kernel", ctypes.c_int32),
     ]
 
 
@@ -127,8 +127,11 @@ def hd_default_opts() -> hd_opts:
     return o
 
 
+SWEEP_KERNELS = {"split": 0, "fused": 1}
+
+
 def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=50, hist_dr=1e-3,
-              cell_min=2.0, block_threads=128) -> hd_opts:
+              cell_min=2.0, block_threads=128, sweep_kernel="split") -> hd_opts:
     o = hd_default_opts()
     o.precision = PRECISIONS.get(precision, precision)
     o.lattice = LATTICES.get(lattice, lattice)
@@ -137,6 +140,7 @@ def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=5
     o.hist_dr = float(hist_dr)
     o.cell_min = float(cell_min)
     o.block_threads = int(block_threads)
+    o.sweep_kernel = SWEEP_KERNELS.get(sweep_kernel, sweep_kernel)
     return o
 
 
@@ -233,7 +237,7 @@ def hd_stats(h):
     return a, b
 
 
-KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions"]
+KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions", "sweep"]
 
 
 def hd_profile(h, enable: bool):
@@ -252,8 +256,9 @@ class HardDisks:
     """Convenience owner of one context (R >= 1 replicas)."""
 
     def __init__(self, N, eta, delta, seed, sigma=1.0, precision="fp64", lattice="square", trials_per_cell=0,
-                 hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128):
-        opts = make_opts(precision, lattice, trials_per_cell, hist_bins, hist_dr, cell_min, block_threads)
+                 hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128, sweep_kernel="split"):
+        opts = make_opts(precision, lattice, trials_per_cell, hist_bins, hist_dr, cell_min, block_threads,
+                         sweep_kernel)
         if np.ndim(N) == 0:
             self.h = hd_init(N, eta, sigma, delta, seed, opts)
         else:

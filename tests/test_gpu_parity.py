@@ -32,9 +32,10 @@ def hd():
     return hd
 
 
-def make_pair(hd, oracle_mod, form, N, eta, delta, seed, lattice="square", nt=0, cell_min=2.0, K=50, dr=1e-3):
+def make_pair(hd, oracle_mod, form, N, eta, delta, seed, lattice="square", nt=0, cell_min=2.0, K=50, dr=1e-3,
+              kernel="split"):
     g = hd.HardDisks(N, eta, delta, seed, precision=form, lattice=lattice, trials_per_cell=nt, cell_min=cell_min,
-                     hist_bins=K, hist_dr=dr)
+                     hist_bins=K, hist_dr=dr, sweep_kernel=kernel)
     o = oracle_mod.OracleChain(N, eta, delta, seed, form=form, lattice=lattice, nt=nt, cell_min=cell_min)
     return g, o
 
@@ -45,10 +46,13 @@ def assert_same_state(g, o):
     assert np.array_equal(g.positions(), o.positions())
 
 
+@pytest.mark.parametrize("kernel", ["fused", "split"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_chain_bit_exact(hd, oracle_mod, form, case):
-    g, o = make_pair(hd, oracle_mod, form, **CASES[case])
+def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
+    """Both sweep kernels: one launch per sweep with shared-memory tiles, and
+    a rebuild launch plus four colour-pass launches."""
+    g, o = make_pair(hd, oracle_mod, form, kernel=kernel, **CASES[case])
     geo, ogeo = g.geometry(), o.geometry()
     assert geo["m"] == ogeo["m"] and geo["L"] == ogeo["L"] and geo["trials_per_cell"] == ogeo["nt"]
     assert_same_state(g, o)  # the initial lattice
@@ -59,10 +63,11 @@ def test_chain_bit_exact(hd, oracle_mod, form, case):
     g.close()
 
 
+@pytest.mark.parametrize("kernel", ["fused", "split"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
-def test_chunk_boundary(hd, oracle_mod, form):
+def test_chunk_boundary(hd, oracle_mod, form, kernel):
     """More sweeps in one call than one draw table holds (256)."""
-    g, o = make_pair(hd, oracle_mod, form, 256, 0.70, 0.1, 21)
+    g, o = make_pair(hd, oracle_mod, form, 256, 0.70, 0.1, 21, kernel=kernel)
     g.sweep(300)
     o.sweep(300)
     assert_same_state(g, o)
@@ -115,6 +120,7 @@ def test_psi6_low_density_ring_search(hd, oracle_mod, form):
 def test_set_positions_roundtrip(hd, oracle_mod, form):
     g, o = make_pair(hd, oracle_mod, form, 400, 0.65, 0.15, 2)
     rng = np.random.default_rng(0)
+    g.sweep(30)
     o.sweep(30)
     xy = o.positions() + rng.integers(-2, 3, size=(400, 2)) * o.geometry()["L"]  # periodic images
     g.set_positions(xy)
@@ -167,12 +173,13 @@ def test_full_size_config2(hd, oracle_mod, form):
     assert np.array_equal(hist[0], o.histogram(50, 1e-3))
 
 
+@pytest.mark.parametrize("kernel", ["fused", "split"])
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
-def test_full_size_config3(hd, oracle_mod, form):
+def test_full_size_config3(hd, oracle_mod, form, kernel):
     """N = 1024^2 at eta = 0.716 (coexistence), the benchmark workload: whole
     state, histogram and every psi_j compared after three sweeps."""
     N = 1024 * 1024
-    g, o = make_pair(hd, oracle_mod, form, N, 0.716, 0.1, 1)
+    g, o = make_pair(hd, oracle_mod, form, N, 0.716, 0.1, 1, kernel=kernel)
     g.sweep(3)
     o.sweep(3)
     assert_same_state(g, o)
