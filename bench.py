@@ -162,10 +162,11 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     S = args.sweeps_per_step
 
+    # one step = one graph launch: S sweeps + pressure and Psi_6 recorded on the device
+    sysg.series_reserve(warmup + steps + 8)
+
     def step():
-        sysg.sweep(S)
-        sysg.pressure(want_hist=False)
-        sysg.psi6(want_local=False)
+        sysg.run(1, S, True)
 
     for _ in range(warmup):
         step()
@@ -198,9 +199,10 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     kt = sysg.kernel_times()
     sysg.profile(False)
     geo = sysg.geometry()
+    series = sysg.series()
     sysg.close()
     return {"ms": ms, "attempts": attempts, "launches": launches, "clocks": clocks, "kernel_times": kt,
-            "geometry": geo}
+            "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None}
 
 
 def time_e2e(args, form, rank, steps):
@@ -328,6 +330,8 @@ def run_ours(args):
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
         "kernel_ms_per_step": {k: v[0] / 2 for k, v in kt.items() if v[1]},
+        "last_measurement": dict(zip(["betaP_over_rho", "g_contact", "psi6_re", "psi6_im"],
+                                     main["last_measurement"] or [])),
         "fp64": fp64,
         "e2e": e2e,
     }

@@ -186,6 +186,32 @@ hd_status hd_get_geometry(hd_ctx *ctx, int32_t r, hd_geometry *g);
 int32_t hd_replicas(const hd_ctx *ctx);
 
 /*
+ * Batched engine for long runs (the equation-of-state scan of Sec. IV.A as
+ * one batch): `steps` steps, each `sweeps_per_step` sweeps (as hd_sweep) and,
+ * when `measure` != 0, one measurement of every replica -- the contact
+ * pressure of hd_pressure and the global Psi_6 of hd_psi6 -- appended on the
+ * device to a series (no host synchronisation).  Each distinct step is
+ * captured once as a CUDA graph and replayed (directly launched while
+ * profiling is enabled).  Asynchronous on the context stream.  R <= 1024.
+ * Errors: HD_ERR_ARG for negative counts or an empty step; HD_ERR_REACH as
+ * hd_pressure when measuring.
+ */
+hd_status hd_run(hd_ctx *ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure);
+
+/* Capacity of the measurement series in steps [4096, allocated by the first
+ * measuring hd_run]; reserving clears the series.  A full series keeps its
+ * first entries and drops later ones. */
+hd_status hd_series_reserve(hd_ctx *ctx, int64_t steps);
+
+/* Copy up to max_steps recorded steps to out[n][R][4] = (beta P / rho,
+ * g(2 sigma+), Re Psi_6, Im Psi_6); *n_steps receives the number copied.
+ * Synchronises. */
+hd_status hd_series(hd_ctx *ctx, int64_t *n_steps, double *out, int64_t max_steps);
+
+/* Forget the recorded steps (asynchronous). */
+hd_status hd_series_clear(hd_ctx *ctx);
+
+/*
  * Instrumentation (no counterpart in the paper).  The library counts every
  * kernel it launches, by class.  With profiling enabled it also brackets each
  * launch with CUDA events on the context stream; hd_kernel_times then

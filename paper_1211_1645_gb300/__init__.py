@@ -9,11 +9,13 @@ binding of that library (``hd``) and its build step (``build``).
 """
 from . import build
 from .hd import (HD_FIXED32, HD_FP64, HDError, HardDisks, hd_batch_init, hd_destroy, hd_get_geometry, hd_init,
-                 hd_positions, hd_positions_device, hd_pressure, hd_psi6, hd_replicas, hd_set_positions,
-                 hd_set_stream, hd_stats, hd_sweep, load, make_opts)
+                 hd_kernel_times, hd_positions, hd_positions_device, hd_pressure, hd_profile, hd_psi6, hd_replicas,
+                 hd_run, hd_series, hd_series_clear, hd_series_reserve, hd_set_positions, hd_set_stream, hd_stats,
+                 hd_sweep, load, make_opts)
 
 __all__ = [
     "build", "load", "make_opts", "HardDisks", "HDError", "HD_FP64", "HD_FIXED32", "hd_init", "hd_batch_init",
     "hd_destroy", "hd_sweep", "hd_pressure", "hd_psi6", "hd_positions", "hd_positions_device",
-    "hd_set_positions", "hd_stats", "hd_get_geometry", "hd_replicas", "hd_set_stream",
+    "hd_set_positions", "hd_stats", "hd_get_geometry", "hd_replicas", "hd_set_stream", "hd_run", "hd_series",
+    "hd_series_reserve", "hd_series_clear", "hd_profile", "hd_kernel_times",
 ]

@@ -71,6 +71,26 @@ struct hd_ctx {
     std::vector<cudaEvent_t> ev;    // pool, used in start/stop pairs
     std::vector<int> ev_class;      // class of each pending pair
     size_t ev_used = 0;
+    // graph-captured steps (hd_run): one executable graph per (sweeps per step,
+    // measure, starting buffer parity), with its kernel tallies
+    struct StepGraph {
+        int sweeps;
+        bool measure;
+        int parity;
+        cudaGraphExec_t exec;
+        int64_t launches[HD_KERNEL_CLASSES];
+    };
+    std::vector<StepGraph> graphs;
+    cudaStream_t capture_stream = nullptr;
+    double* series = nullptr;       // [cap][R][4]: beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6
+    int64_t* series_len = nullptr;  // device counter of recorded steps
+    int64_t series_cap = 0;
+
+    hd::LaunchCfg cfg(cudaStream_t s) const {
+        hd::LaunchCfg c = cfg();
+        c.stream = s;
+        return c;
+    }
 
     hd::LaunchCfg cfg() const {
         hd::LaunchCfg c;
@@ -262,8 +282,17 @@ hd_status check_flags(hd_ctx* ctx) {
     return HD_OK;
 }
 
+void drop_graphs(hd_ctx* ctx) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
 void free_ctx(hd_ctx* ctx) {
     if (!ctx) return;
+    drop_graphs(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->series) cudaFree(ctx->series);
+    if (ctx->series_len) cudaFree(ctx->series_len);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
@@ -283,11 +312,12 @@ bool prof_flush(hd_ctx* ctx) {
     return true;
 }
 
-// Enqueue one kernel launch of class `cls`, bracketed by events when profiling.
+// Enqueue one kernel launch of class `cls`, bracketed by events when
+// profiling (never while a graph is being captured).
 template <class F>
-cudaError_t launch(hd_ctx* ctx, int cls, F&& f) {
+cudaError_t launch(hd_ctx* ctx, int cls, F&& f, bool capturing = false) {
     ctx->launches[cls] += 1;
-    if (!ctx->profiling) return f();
+    if (!ctx->profiling || capturing) return f();
     if (ctx->ev_used + 2 > ctx->ev.size() && !prof_flush(ctx)) return cudaErrorUnknown;
     cudaError_t e = cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream);
     if (e != cudaSuccess) return e;
@@ -297,6 +327,74 @@ cudaError_t launch(hd_ctx* ctx, int cls, F&& f) {
     ctx->ev_class.push_back(cls);
     ctx->ev_used += 2;
     return e;
+}
+
+// Enqueue n sweeps on stream s (draw tables of up to kMaxChunk sweeps, then
+// per sweep either one fused launch or a rebuild and four colour passes).
+cudaError_t enqueue_sweeps(hd_ctx* ctx, cudaStream_t s, int64_t n, bool capturing) {
+    const hd::LaunchCfg c = ctx->cfg(s);
+    int64_t left = n;
+    cudaError_t e = cudaSuccess;
+    while (left > 0 && e == cudaSuccess) {
+        const int nc = int(std::min<int64_t>(left, hd::kMaxChunk));
+        e = launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); },
+                   capturing);
+        for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
+            if (ctx->fused) {
+                e = launch(ctx, HD_K_SWEEP, [&] {
+                    return hd::launch_sweep_fused(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1],
+                                                  ctx->counters, ctx->err);
+                }, capturing);
+                ctx->cur ^= 1;
+            } else {
+                e = launch(ctx, HD_K_REBUILD, [&] {
+                    return hd::launch_rebuild(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->err);
+                }, capturing);
+                ctx->cur ^= 1;
+                for (int p = 0; p < 4 && e == cudaSuccess; ++p)
+                    e = launch(ctx, HD_K_PASS, [&] {
+                        return hd::launch_pass(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters);
+                    }, capturing);
+            }
+        }
+        left -= nc;
+    }
+    return e;
+}
+
+// Enqueue the contact histogram and the pressure fit on stream s.
+cudaError_t enqueue_pressure(hd_ctx* ctx, cudaStream_t s, bool capturing) {
+    const hd::LaunchCfg c = ctx->cfg(s);
+    cudaError_t e = cudaMemsetAsync(ctx->hist, 0, sizeof(unsigned long long) * size_t(ctx->R) * ctx->K, s);
+    if (e != cudaSuccess) return e;
+    const hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF};
+    e = launch(ctx, HD_K_HIST, [&] { return hd::launch_hist(c, h, ctx->buf[ctx->cur], ctx->hist); }, capturing);
+    if (e != cudaSuccess) return e;
+    return launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->hist, ctx->fit); }, capturing);
+}
+
+// Enqueue psi_6 (local field into psi_local when `local`) and its reduction.
+cudaError_t enqueue_psi6(hd_ctx* ctx, cudaStream_t s, bool local, bool capturing) {
+    const hd::LaunchCfg c = ctx->cfg(s);
+    cudaError_t e = launch(ctx, HD_K_PSI6, [&] {
+        return hd::launch_psi6(c, ctx->buf[ctx->cur], local ? ctx->psi_local : nullptr, ctx->psi_part, ctx->err);
+    }, capturing);
+    if (e != cudaSuccess) return e;
+    return launch(ctx, HD_K_PSI6_REDUCE, [&] { return hd::launch_psi6_reduce(c, ctx->psi_part, ctx->psi_res); },
+                  capturing);
+}
+
+// One hd_run step: sweeps, then (optionally) a measurement appended to the
+// device series.
+cudaError_t enqueue_step(hd_ctx* ctx, cudaStream_t s, int sweeps, bool measure, bool capturing) {
+    cudaError_t e = enqueue_sweeps(ctx, s, sweeps, capturing);
+    if (e != cudaSuccess || !measure) return e;
+    e = enqueue_pressure(ctx, s, capturing);
+    if (e != cudaSuccess) return e;
+    e = enqueue_psi6(ctx, s, false, capturing);
+    if (e != cudaSuccess) return e;
+    return hd::launch_record(ctx->cfg(s), ctx->fit, ctx->psi_res, ctx->series, ctx->series_len, ctx->series_cap,
+                             ctx->err);
 }
 
 }  // namespace
@@ -532,28 +630,7 @@ hd_status hd_set_stream(hd_ctx* ctx, void* stream) {
 hd_status hd_sweep(hd_ctx* ctx, int64_t n) {
     if (!ctx || n < 0) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
-    const hd::LaunchCfg c = ctx->cfg();
-    int64_t left = n;
-    while (left > 0) {
-        const int nc = int(std::min<int64_t>(left, hd::kMaxChunk));
-        HD_CK(ctx, launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); }));
-        for (int j = 1; j <= nc && ctx->fused; ++j) {
-            HD_CK(ctx, launch(ctx, HD_K_SWEEP, [&] {
-                return hd::launch_sweep_fused(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1],
-                                              ctx->counters, ctx->err);
-            }));
-            ctx->cur ^= 1;
-        }
-        for (int j = 1; j <= nc && !ctx->fused; ++j) {
-            HD_CK(ctx, launch(ctx, HD_K_REBUILD, [&] {
-                return hd::launch_rebuild(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->err);
-            }));
-            ctx->cur ^= 1;
-            for (int p = 0; p < 4; ++p)
-                HD_CK(ctx, launch(ctx, HD_K_PASS, [&] { return hd::launch_pass(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters); }));
-        }
-        left -= nc;
-    }
+    HD_CK(ctx, enqueue_sweeps(ctx, ctx->stream, n, false));
     for (auto& s : ctx->sweeps) s += n;
     return HD_OK;
 }
@@ -563,11 +640,7 @@ hd_status hd_pressure(hd_ctx* ctx, double* betaP_over_rho, double* g_contact, ui
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     for (const Rep& r : ctx->reps)
         if (2 * r.hist_R + 1 > r.m) return HD_ERR_REACH;
-    const hd::LaunchCfg c = ctx->cfg();
-    HD_CK(ctx, cudaMemsetAsync(ctx->hist, 0, sizeof(unsigned long long) * size_t(ctx->R) * ctx->K, ctx->stream));
-    hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF};
-    HD_CK(ctx, launch(ctx, HD_K_HIST, [&] { return hd::launch_hist(c, h, ctx->buf[ctx->cur], ctx->hist); }));
-    HD_CK(ctx, launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->hist, ctx->fit); }));
+    HD_CK(ctx, enqueue_pressure(ctx, ctx->stream, false));
     std::vector<double> res(size_t(4 * ctx->R));
     HD_CK(ctx, cudaMemcpyAsync(res.data(), ctx->fit, res.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (hist)
@@ -586,11 +659,7 @@ hd_status hd_pressure(hd_ctx* ctx, double* betaP_over_rho, double* g_contact, ui
 hd_status hd_psi6(hd_ctx* ctx, double* re, double* im, double* local) {
     if (!ctx) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
-    const hd::LaunchCfg c = ctx->cfg();
-    HD_CK(ctx, launch(ctx, HD_K_PSI6, [&] {
-        return hd::launch_psi6(c, ctx->buf[ctx->cur], local ? ctx->psi_local : nullptr, ctx->psi_part, ctx->err);
-    }));
-    HD_CK(ctx, launch(ctx, HD_K_PSI6_REDUCE, [&] { return hd::launch_psi6_reduce(c, ctx->psi_part, ctx->psi_res); }));
+    HD_CK(ctx, enqueue_psi6(ctx, ctx->stream, local != nullptr, false));
     std::vector<double> res(size_t(2 * ctx->R));
     HD_CK(ctx, cudaMemcpyAsync(res.data(), ctx->psi_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));
@@ -692,6 +761,101 @@ hd_status hd_get_geometry(hd_ctx* ctx, int32_t r, hd_geometry* g) {
 }
 
 int32_t hd_replicas(const hd_ctx* ctx) { return ctx ? ctx->R : 0; }
+
+hd_status hd_series_reserve(hd_ctx* ctx, int64_t steps) {
+    if (!ctx || steps < 1) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);  // they hold the old series pointers
+    if (ctx->series) cudaFree(ctx->series);
+    ctx->series = nullptr;
+    ctx->series_cap = 0;
+    if (!ctx->series_len) HD_CK(ctx, cudaMalloc(&ctx->series_len, sizeof(int64_t)));
+    HD_CK(ctx, cudaMalloc(&ctx->series, sizeof(double) * 4 * size_t(ctx->R) * size_t(steps)));
+    HD_CK(ctx, cudaMemset(ctx->series_len, 0, sizeof(int64_t)));
+    ctx->series_cap = steps;
+    return HD_OK;
+}
+
+hd_status hd_run(hd_ctx* ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure) {
+    if (!ctx || steps < 0 || sweeps_per_step < 0 || (sweeps_per_step == 0 && !measure) || ctx->R > 1024)
+        return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    if (measure)
+        for (const Rep& r : ctx->reps)
+            if (2 * r.hist_R + 1 > r.m) return HD_ERR_REACH;
+    if (measure && !ctx->series) {
+        const hd_status s = hd_series_reserve(ctx, 4096);
+        if (s != HD_OK) return s;
+    }
+    const bool meas = measure != 0;
+    if (ctx->profiling) {  // direct launches, so that every kernel is timed
+        for (int64_t k = 0; k < steps; ++k) HD_CK(ctx, enqueue_step(ctx, ctx->stream, sweeps_per_step, meas, false));
+    } else {
+        if (!ctx->capture_stream) HD_CK(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        for (int64_t k = 0; k < steps; ++k) {
+            const int parity = ctx->cur;
+            hd_ctx::StepGraph* g = nullptr;
+            for (auto& x : ctx->graphs)
+                if (x.sweeps == sweeps_per_step && x.measure == meas && x.parity == parity) g = &x;
+            if (!g) {
+                hd_ctx::StepGraph ng;
+                ng.sweeps = sweeps_per_step;
+                ng.measure = meas;
+                ng.parity = parity;
+                int64_t before[HD_KERNEL_CLASSES];
+                std::memcpy(before, ctx->launches, sizeof(before));
+                cudaGraph_t graph = nullptr;
+                HD_CK(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+                const cudaError_t ce = enqueue_step(ctx, ctx->capture_stream, sweeps_per_step, meas, true);
+                const cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &graph);
+                ctx->cur = parity;  // capture only recorded the launches
+                for (int c = 0; c < HD_KERNEL_CLASSES; ++c) {
+                    ng.launches[c] = ctx->launches[c] - before[c];
+                    ctx->launches[c] = before[c];
+                }
+                if (ce != cudaSuccess || ee != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return fail_cuda(ctx);
+                }
+                const cudaError_t ie = cudaGraphInstantiate(&ng.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ie != cudaSuccess) return fail_cuda(ctx);
+                ctx->graphs.push_back(ng);
+                g = &ctx->graphs.back();
+            }
+            HD_CK(ctx, cudaGraphLaunch(g->exec, ctx->stream));
+            for (int c = 0; c < HD_KERNEL_CLASSES; ++c) ctx->launches[c] += g->launches[c];
+            if (sweeps_per_step & 1) ctx->cur ^= 1;
+        }
+    }
+    for (auto& s : ctx->sweeps) s += steps * sweeps_per_step;
+    return HD_OK;
+}
+
+hd_status hd_series(hd_ctx* ctx, int64_t* n_steps, double* out, int64_t max_steps) {
+    if (!ctx || !n_steps || max_steps < 0) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    *n_steps = 0;
+    if (!ctx->series) return HD_OK;
+    int64_t len = 0;
+    HD_CK(ctx, cudaMemcpyAsync(&len, ctx->series_len, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const hd_status f = check_flags(ctx);
+    if (f != HD_OK) return f;
+    const int64_t n = std::min(len, max_steps);
+    if (out && n > 0)
+        HD_CK(ctx, cudaMemcpy(out, ctx->series, sizeof(double) * 4 * size_t(ctx->R) * size_t(n), cudaMemcpyDeviceToHost));
+    *n_steps = n;
+    return HD_OK;
+}
+
+hd_status hd_series_clear(hd_ctx* ctx) {
+    if (!ctx) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    if (ctx->series_len) HD_CK(ctx, cudaMemsetAsync(ctx->series_len, 0, sizeof(int64_t), ctx->stream));
+    return HD_OK;
+}
 
 hd_status hd_profile(hd_ctx* ctx, int32_t enable) {
     if (!ctx) return HD_ERR_ARG;

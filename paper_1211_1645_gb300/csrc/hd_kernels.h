@@ -50,5 +50,9 @@ cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, un
 cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res);
 cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err);
 cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res);
+// Append (beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6) of every replica to
+// series[len] and advance len (bounded by cap; a full series sets err bit 4).
+cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* psi, double* series,
+                          int64_t* len, int64_t cap, int* err);
 
 }  // namespace hd

@@ -421,6 +421,30 @@ cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, doub
     return cudaGetLastError();
 }
 
+__global__ void k_record(int R, const double* __restrict__ fit, const double* __restrict__ psi,
+                         double* __restrict__ series, int64_t* __restrict__ len, int64_t cap, int* __restrict__ err) {
+    const int64_t idx = *len;
+    const int r = threadIdx.x;
+    if (r < R && idx < cap) {
+        double* row = series + (size_t(idx) * R + r) * 4;
+        row[0] = fit[4 * r];
+        row[1] = fit[4 * r + 1];
+        row[2] = psi[2 * r];
+        row[3] = psi[2 * r + 1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (idx < cap) *len = idx + 1;
+        else atomicOr(err, 4);
+    }
+}
+
+cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* psi, double* series, int64_t* len,
+                          int64_t cap, int* err) {
+    k_record<<<1, ((c.R + 31) / 32) * 32, 0, c.stream>>>(c.R, fit, psi, series, len, cap, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res) {
     k_psi6_reduce<<<c.R, 256, 0, c.stream>>>(c.reps, c.R, c.blocks_cell, partial, res);
     return cudaGetLastError();

@@ -98,6 +98,10 @@ def load(path: str | None = None):
             "hd_get_geometry": (S, [P, c.c_int32, c.POINTER(hd_geometry)]),
             "hd_replicas": (c.c_int32, [P]),
             "hd_profile": (S, [P, c.c_int32]),
+            "hd_run": (S, [P, c.c_int64, c.c_int32, c.c_int32]),
+            "hd_series_reserve": (S, [P, c.c_int64]),
+            "hd_series": (S, [P, P, P, c.c_int64]),
+            "hd_series_clear": (S, [P]),
             "hd_kernel_times": (S, [P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -237,6 +241,30 @@ def hd_stats(h):
     return a, b
 
 
+def hd_run(h, steps: int, sweeps_per_step: int, measure: bool = True):
+    _check(load().hd_run(h, int(steps), int(sweeps_per_step), int(bool(measure))), "hd_run")
+
+
+def hd_series_reserve(h, steps: int):
+    _check(load().hd_series_reserve(h, int(steps)), "hd_series_reserve")
+
+
+def hd_series(h, max_steps: int = 1 << 20):
+    """Recorded steps as an array [n, R, 4]: beta P / rho, g(2 sigma+), Re, Im Psi_6."""
+    R = hd_replicas(h)
+    n = np.zeros(1, np.int64)
+    cap = int(max_steps)
+    probe = ctypes.c_int64(0)
+    _check(load().hd_series(h, ctypes.byref(probe), None, cap), "hd_series")
+    out = np.zeros((max(1, int(probe.value)), R, 4), np.float64)
+    _check(load().hd_series(h, _ptr(n), _ptr(out), int(probe.value)), "hd_series")
+    return out[: int(n[0])]
+
+
+def hd_series_clear(h):
+    _check(load().hd_series_clear(h), "hd_series_clear")
+
+
 KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions", "sweep"]
 
 
@@ -300,6 +328,18 @@ class HardDisks:
 
     def set_stream(self, stream_ptr):
         hd_set_stream(self.h, stream_ptr)
+
+    def run(self, steps, sweeps_per_step, measure=True):
+        hd_run(self.h, steps, sweeps_per_step, measure)
+
+    def series(self):
+        return hd_series(self.h)
+
+    def series_reserve(self, steps):
+        hd_series_reserve(self.h, steps)
+
+    def series_clear(self):
+        hd_series_clear(self.h)
 
     def profile(self, enable=True):
         hd_profile(self.h, enable)

@@ -237,3 +237,55 @@ def test_overflow_rejected_on_set_positions(hd):
     with pytest.raises(HDError) as e:
         g.set_positions(xy)
     assert e.value.status == HD_ERR_OVERFLOW
+
+
+@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_graph_engine_series(hd, oracle_mod, form, kernel):
+    """hd_run: graph-captured steps of 7 sweeps (odd, so both buffer parities
+    are captured) with a device-side measurement per step; the series must
+    equal the oracle's pressure and Psi_6 after each step, and the chain must
+    continue exactly."""
+    g, o = make_pair(hd, oracle_mod, form, 400, 0.70, 0.1, 31, kernel=kernel)
+    g.run(3, 7, measure=True)
+    ser = g.series()
+    assert ser.shape == (3, 1, 4)
+    L = o.geometry()["L"]
+    for k in range(3):
+        o.sweep(7)
+        h = o.histogram(50, 1e-3)
+        want = oracle_mod.contact_pressure(h, 400, L, o.realised_dr(1e-3))
+        _, rglob = o.psi6()
+        assert abs(ser[k, 0, 0] - want["betaP_over_rho"]) <= 1e-12 * want["betaP_over_rho"]
+        assert abs(ser[k, 0, 1] - want["g0"]) <= 1e-12 * max(1.0, abs(want["g0"]))
+        assert abs(complex(ser[k, 0, 2], ser[k, 0, 3]) - rglob) <= 1e-12
+    assert_same_state(g, o)
+    g.run(2, 7, measure=False)
+    o.sweep(14)
+    assert_same_state(g, o)
+    assert g.series().shape[0] == 3
+    g.series_clear()
+    assert g.series().shape[0] == 0
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_graph_engine_batched(hd, oracle_mod, form):
+    Ns = [20 ** 2, 16 ** 2, 24 ** 2]
+    etas = [0.70, 0.71, 0.705]
+    g = hd.HardDisks(Ns, etas, [0.1] * 3, [7, 8, 9], precision=form)
+    os_ = [oracle_mod.OracleChain(n, e, 0.1, s, form=form) for n, e, s in zip(Ns, etas, [7, 8, 9])]
+    g.run(2, 10, measure=True)
+    ser = g.series()
+    assert ser.shape == (2, 3, 4)
+    for k in range(2):
+        for r, o in enumerate(os_):
+            o.sweep(10)
+            want = oracle_mod.contact_pressure(o.histogram(50, 1e-3), Ns[r], o.geometry()["L"], o.realised_dr(1e-3))
+            assert abs(ser[k, r, 0] - want["betaP_over_rho"]) <= 1e-12 * want["betaP_over_rho"]
+            _, rglob = o.psi6()
+            assert abs(complex(ser[k, r, 2], ser[k, r, 3]) - rglob) <= 1e-12
+    xy = g.positions()
+    off = 0
+    for r, o in enumerate(os_):
+        assert np.array_equal(xy[off:off + Ns[r]], o.positions())
+        off += Ns[r]
