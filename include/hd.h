@@ -212,6 +212,28 @@ hd_status hd_series(hd_ctx *ctx, int64_t *n_steps, double *out, int64_t max_step
 hd_status hd_series_clear(hd_ctx *ctx);
 
 /*
+ * Global Psi_6 = (1/N) sum_j psi_j from a per-disk field that the caller
+ * already holds on the device (for instance the local field of hd_psi6,
+ * copied to device memory), for callers that may not allocate device memory
+ * at this point: inside a CUDA stream capture, under a framework that owns
+ * every allocation, or in a loop where an allocation could block or fail.
+ * The paper has no counterpart; it is a deployment variant of the reduction
+ * behind hd_psi6.
+ *   psi_local_device  device array of N (Re, Im) double pairs, by disk id
+ *   N                 1 <= N <= 16,777,216 (4096 blocks of 4096 values);
+ *                     larger N returns HD_ERR_ARG
+ *   out_device        device array of 2 doubles receiving (Re, Im)
+ *   stream            cudaStream_t as void* (NULL: legacy default stream)
+ * The call allocates and frees nothing: its block partial sums live in a
+ * fixed 64 KiB device array of the library, looked up on the first call on
+ * each device (make that first call outside any stream capture).  All calls
+ * share that array, so calls that may overlap on the GPU race and must be
+ * ordered by the caller.  Asynchronous; returns HD_ERR_ARG for NULL pointers
+ * or N out of range, HD_ERR_CUDA if a launch or the lookup fails.
+ */
+hd_status hd_psi6_mean_noalloc(const double *psi_local_device, int64_t N, double *out_device, void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper).  The library counts every
  * kernel it launches, by class.  With profiling enabled it also brackets each
  * launch with CUDA events on the context stream; hd_kernel_times then

@@ -102,6 +102,7 @@ def load(path: str | None = None):
             "hd_series_reserve": (S, [P, c.c_int64]),
             "hd_series": (S, [P, P, P, c.c_int64]),
             "hd_series_clear": (S, [P]),
+            "hd_psi6_mean_noalloc": (S, [P, c.c_int64, P, P]),
             "hd_kernel_times": (S, [P, P, P]),
         }
         for name, (res, args) in sig.items():
