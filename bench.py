@@ -274,6 +274,34 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def kernel_sources_hash():
+    """First 16 hex digits of the sha256 of the CUDA sources (*.cu, *.cuh,
+    *.h of the library, in that order), as recorded beside ncu counters."""
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_1211_1645_gb300", "csrc")
+    files = (sorted(glob.glob(os.path.join(d, "*.cu"))) + sorted(glob.glob(os.path.join(d, "*.cuh")))
+             + sorted(glob.glob(os.path.join(d, "*.h"))))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries,
+    or None when no summary was taken on the current kernel sources."""
+    import glob
+    import re
+    want = kernel_sources_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            mt = re.match(r"\s*traffic (\S+) bytes_per_launch=(\d+) sources=(\w+)", line)
+            if mt and mt.group(1) == f"k_{kernel}" and mt.group(3) == want:
+                return int(mt.group(2))
+    return None
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_setup(args)
@@ -324,7 +352,7 @@ def run_ours(args):
                    "trials_per_cell": geo["trials_per_cell"], "l2": "flushed before each timed step (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top),
                      "kernel": top, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg, "avg_launch_us": top_avg_s * 1e6},
         "gpu_launches": main["launches"],
