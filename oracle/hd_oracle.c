@@ -381,13 +381,26 @@ static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy)
     if (n == 0) return;
     const int64_t *ids = &s->cids[s->cstart[c]];
 
-    /* Fisher-Yates shuffle of the occupants (ascending ids) */
+    /* Fisher-Yates shuffle of the occupants (ascending ids).  The swap words
+     * come from the shuffle stream; in the fixed-point form, whose step uses
+     * only two words of a trial block, the first two swap words are the
+     * unused words 2 and 3 of trial 0's block and the shuffle stream supplies
+     * the rest. */
     int64_t perm[64];
-    uint32_t words[64];
+    uint32_t words[72];
     for (int64_t k = 0; k < n; ++k) perm[k] = k;
-    for (uint32_t blk = 0; 4 * blk < (uint32_t)(n - 1); ++blk) {
+    uint32_t lead = 0;
+    if (s->form == HDO_FIXED && n > 1) {
+        uint32_t ctr[4] = {sweep32, 0u, (uint32_t)c, TAG_TRIAL};
+        uint32_t a[4];
+        hdo_philox4x32_10(ctr, s->key, a);
+        words[0] = a[2];
+        words[1] = a[3];
+        lead = 2;
+    }
+    for (uint32_t blk = 0; lead + 4 * blk < (uint32_t)(n - 1); ++blk) {
         uint32_t ctr[4] = {sweep32, blk, (uint32_t)c, TAG_SHUFFLE};
-        hdo_philox4x32_10(ctr, s->key, &words[4 * blk]);
+        hdo_philox4x32_10(ctr, s->key, &words[lead + 4 * blk]);
     }
     for (int64_t k = n - 1; k >= 1; --k) {
         uint32_t j = bounded(words[n - 1 - k], (uint32_t)(k + 1));

@@ -254,9 +254,30 @@ template <bool FIX, int CAP, class NbrClear>
 __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
                                              NbrClear&& neighbours_clear) {
     uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
+    // The fixed-point step uses two words of a trial block; the other two of
+    // trial 0's block are the first two swap words, so a cell of up to three
+    // occupants needs a single generator call.  The FP64 step uses all four.
+    uint4 u0 = make_uint4(0, 0, 0, 0);
+    if constexpr (FIX) u0 = philox(sweep, 0u, cl, kTagTrial, rep.key0, rep.key1);
     if (n > 1) {
-        uint4 w0 = philox(sweep, 0u, cl, kTagShuffle, rep.key0, rep.key1), w1 = make_uint4(0, 0, 0, 0);
-        if (CAP > 5 && n > 5) w1 = philox(sweep, 1u, cl, kTagShuffle, rep.key0, rep.key1);
+        uint4 w0, w1 = make_uint4(0, 0, 0, 0);
+        if constexpr (FIX) {
+            w0 = make_uint4(u0.z, u0.w, 0u, 0u);
+            if (n > 3) {
+                const uint4 a = philox(sweep, 0u, cl, kTagShuffle, rep.key0, rep.key1);
+                w0.z = a.x;
+                w0.w = a.y;
+                w1 = make_uint4(a.z, a.w, 0u, 0u);
+                if (CAP > 7 && n > 7) {
+                    const uint4 b = philox(sweep, 1u, cl, kTagShuffle, rep.key0, rep.key1);
+                    w1.z = b.x;
+                    w1.w = b.y;
+                }
+            }
+        } else {
+            w0 = philox(sweep, 0u, cl, kTagShuffle, rep.key0, rep.key1);
+            if (CAP > 5 && n > 5) w1 = philox(sweep, 1u, cl, kTagShuffle, rep.key0, rep.key1);
+        }
 #pragma unroll
         for (int k = CAP - 1; k >= 1; --k) {
             if (k < n) {
@@ -270,7 +291,7 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
     }
     uint32_t acc = 0;
     for (int t = 0; t < rep.nt; ++t) {
-        const uint4 u = philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
+        const uint4 u = (FIX && t == 0) ? u0 : philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
         const int slot = int((order >> (4 * (n == 1 ? 0 : t % n))) & 0xFull);
         P2<FIX> me = P[0];
 #pragma unroll
