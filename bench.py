@@ -46,6 +46,7 @@ def parse_args(argv=None):
     p.add_argument("--N", type=int, default=1024 * 1024)
     p.add_argument("--eta", type=float, default=0.716)
     p.add_argument("--delta", type=float, default=0.1)
+    p.add_argument("--cell-min", type=float, default=2.0, help="minimum cell side in sigma (>= 2)")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--form", choices=["fixed", "fp64"], default="fixed")
     p.add_argument("--sweep-kernel", choices=["split", "fused"], default="split")
@@ -157,7 +158,7 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
     sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form,
-                        sweep_kernel=args.sweep_kernel)
+                        sweep_kernel=args.sweep_kernel, cell_min=args.cell_min)
     sysg.set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     S = args.sweeps_per_step
@@ -187,7 +188,9 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     clocks = sampler.stop() if sampler else None
     barrier(world)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    attempts = int(sysg.stats()[0][0]) - att0
+    att1, acc1 = sysg.stats()
+    attempts = int(att1[0]) - att0
+    acceptance = float(acc1[0]) / float(att1[0]) if int(att1[0]) else None
     l1 = sysg.kernel_times()
     launches = sum(l1[k][1] - l0[k][1] for k in l1)
 
@@ -202,7 +205,8 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     series = sysg.series()
     sysg.close()
     return {"ms": ms, "attempts": attempts, "launches": launches, "clocks": clocks, "kernel_times": kt,
-            "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None}
+            "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None,
+            "acceptance": acceptance}
 
 
 def time_e2e(args, form, rank, steps):
@@ -213,7 +217,7 @@ def time_e2e(args, form, rank, steps):
 
     import paper_1211_1645_gb300 as hd
 
-    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form)
+    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form, cell_min=args.cell_min)
     xy = np.ascontiguousarray(sysg.positions())
     S = args.sweeps_per_step
     att0 = int(sysg.stats()[0][0])
@@ -252,7 +256,7 @@ def algorithmic_bytes(kernel, N, m, form):
 def cpu_oracle(args, form, budget_s):
     import oracle
     oracle.build()
-    o = oracle.OracleChain(args.N, args.eta, args.delta, args.seed, form=form)
+    o = oracle.OracleChain(args.N, args.eta, args.delta, args.seed, form=form, cell_min=args.cell_min)
     a0, _ = o.stats()
     t0 = time.perf_counter()
     sweeps = 0
@@ -349,7 +353,8 @@ def run_ours(args):
         "config": {"workload": f"MPMC hard disks N={args.N} eta={args.eta} delta={args.delta}, "
                                f"{args.form} form, {args.sweeps_per_step} sweeps + 1 pressure/psi6 measurement per step",
                    "N": args.N, "eta": args.eta, "sweeps_per_step": args.sweeps_per_step, "cells_per_side": geo["m"],
-                   "trials_per_cell": geo["trials_per_cell"], "l2": "flushed before each timed step (256 MB write)",
+                   "trials_per_cell": geo["trials_per_cell"], "cell_side": geo["w"],
+                   "acceptance": main["acceptance"], "l2": "flushed before each timed step (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top),

@@ -72,6 +72,15 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Programmatic dependent launch: allow the next kernel of the stream to be
+// scheduled once every block of this one has started, and wait until the
+// previous kernel has completed and its memory is visible.  Both are no-ops
+// when the launch did not opt in.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // floor(word * n / 2^32): an integer in [0, n).
 __device__ __forceinline__ uint32_t bounded(uint32_t word, uint32_t n) { return __umulhi(word, n); }
 

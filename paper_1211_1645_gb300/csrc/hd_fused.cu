@@ -77,6 +77,7 @@ k_sweep_fused(const Rep* __restrict__ reps, int R, const Frame* __restrict__ tab
     uint8_t* s_cnt = smem + F::kPosBytes + F::kPidBytes;                                // [NC]
     uint16_t* s_list = reinterpret_cast<uint16_t*>(s_cnt + F::kCntBytes);              // [2][H*H]
     __shared__ int s_len[2];
+    pdl_begin();
 
     const int r = find_rep<kGridTile>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
@@ -264,9 +265,9 @@ static cudaError_t fused_t(const LaunchCfg& c, const Frame* table, int j, CellBu
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_sweep_fused<FIX, CAP, T, NT><<<c.blocks_tile, NT, smem, c.stream>>>(
-        c.reps, c.R, table, j, a.cnt, (const P2<FIX>*)a.pos, a.pid, b.cnt, (P2<FIX>*)b.pos, b.pid, counters, err);
-    return cudaGetLastError();
+    return launch_k(k_sweep_fused<FIX, CAP, T, NT>, dim3(c.blocks_tile), dim3(NT), smem, c.stream, c.reps, c.R, table,
+                    j, (const uint8_t*)a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt, (P2<FIX>*)b.pos,
+                    b.pid, counters, err);
 }
 
 cudaError_t launch_sweep_fused(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,

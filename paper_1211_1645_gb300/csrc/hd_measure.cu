@@ -29,6 +29,7 @@ k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ ed
        const long long* __restrict__ edgesF, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
        const int32_t* __restrict__ pid, unsigned long long* __restrict__ hist) {
     extern __shared__ unsigned int s_bins[];
+    pdl_begin();
     for (int b = threadIdx.x; b < K; b += blockDim.x) s_bins[b] = 0u;
     __syncthreads();
     const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
@@ -92,21 +93,28 @@ k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ ed
 // ---------------------------------------------------------------------------
 // g(r) normalisation (Eq. 2, p = N^2 / 2), least-squares quartic in
 // t = (r - 2 sigma) / (K dr) by Householder QR, value at contact, and the
-// contact-value pressure (Eq. 4).  One block per replica, one thread works.
+// contact-value pressure (Eq. 4).  One warp per replica: the K rows are
+// spread over the lanes and every column norm and dot product is a warp sum.
 // res[4r + 0..3] = beta P / rho, g(2 sigma+), P* = beta P (2 sigma)^2, eta.
 // ---------------------------------------------------------------------------
-__global__ void k_fit(const Rep* __restrict__ reps, int K, const unsigned long long* __restrict__ hist,
-                      double* __restrict__ res) {
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K,
+                                            const unsigned long long* __restrict__ hist, double* __restrict__ res) {
+    pdl_begin();
     __shared__ double A[kMaxFitBins * 5];
     __shared__ double b[kMaxFitBins];
-    if (threadIdx.x != 0) return;
-    const int r = blockIdx.x;
+    const int r = blockIdx.x, lane = threadIdx.x;
     const Rep& rep = reps[r];
     const double PI = 3.14159265358979323846;
     const double V = __dmul_rn(rep.Lm, rep.Lm);
     const double p = __dmul_rn(__dmul_rn(double(rep.N), double(rep.N)), 0.5);
     const double dr = rep.dr;
-    for (int k = 0; k < K; ++k) {
+    for (int k = lane; k < K; k += 32) {
         const double rk = __dadd_rn(2.0, __dmul_rn(__dadd_rn(double(k), 0.5), dr));
         const double shell = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, PI), rk), dr), V);
         b[k] = __ddiv_rn(__ddiv_rn(double(hist[size_t(r) * K + k]), p), shell);
@@ -117,28 +125,36 @@ __global__ void k_fit(const Rep* __restrict__ reps, int K, const unsigned long l
             tp = __dmul_rn(tp, t);
         }
     }
+    __syncwarp();
     // Householder triangularisation of the K x 5 design matrix, applied to b
     for (int j = 0; j < 5; ++j) {
-        double nrm2 = 0.0;
-        for (int i = j; i < K; ++i) nrm2 = __dadd_rn(nrm2, __dmul_rn(A[i * 5 + j], A[i * 5 + j]));
+        double part = 0.0;
+        for (int i = j + lane; i < K; i += 32) part = __dadd_rn(part, __dmul_rn(A[i * 5 + j], A[i * 5 + j]));
+        const double nrm2 = warp_sum(part);
         const double nrm = sqrt(nrm2);
         if (nrm == 0.0) continue;
-        const double alpha = A[j * 5 + j] > 0.0 ? -nrm : nrm;
-        const double v0 = __dsub_rn(A[j * 5 + j], alpha);
-        const double vtv = __dadd_rn(__dsub_rn(nrm2, __dmul_rn(A[j * 5 + j], A[j * 5 + j])), __dmul_rn(v0, v0));
-        A[j * 5 + j] = v0;  // v = (v0, A[j+1.., j])
-        for (int q = j + 1; q < 5; ++q) {
-            double d = 0.0;
-            for (int i = j; i < K; ++i) d = __dadd_rn(d, __dmul_rn(A[i * 5 + j], A[i * 5 + q]));
-            const double s = __ddiv_rn(__dmul_rn(2.0, d), vtv);
-            for (int i = j; i < K; ++i) A[i * 5 + q] = __dsub_rn(A[i * 5 + q], __dmul_rn(s, A[i * 5 + j]));
+        const double ajj = A[j * 5 + j];
+        const double alpha = ajj > 0.0 ? -nrm : nrm;
+        const double v0 = __dsub_rn(ajj, alpha);
+        const double vtv = __dadd_rn(__dsub_rn(nrm2, __dmul_rn(ajj, ajj)), __dmul_rn(v0, v0));
+        __syncwarp();
+        if (lane == 0) A[j * 5 + j] = v0;  // v = (v0, A[j+1.., j])
+        __syncwarp();
+        for (int q = j + 1; q <= 5; ++q) {  // q == 5 is the right-hand side b
+            double dp = 0.0;
+            for (int i = j + lane; i < K; i += 32)
+                dp = __dadd_rn(dp, __dmul_rn(A[i * 5 + j], q < 5 ? A[i * 5 + q] : b[i]));
+            const double sc = __ddiv_rn(__dmul_rn(2.0, warp_sum(dp)), vtv);
+            for (int i = j + lane; i < K; i += 32) {
+                if (q < 5) A[i * 5 + q] = __dsub_rn(A[i * 5 + q], __dmul_rn(sc, A[i * 5 + j]));
+                else b[i] = __dsub_rn(b[i], __dmul_rn(sc, A[i * 5 + j]));
+            }
+            __syncwarp();
         }
-        double d = 0.0;
-        for (int i = j; i < K; ++i) d = __dadd_rn(d, __dmul_rn(A[i * 5 + j], b[i]));
-        const double s = __ddiv_rn(__dmul_rn(2.0, d), vtv);
-        for (int i = j; i < K; ++i) b[i] = __dsub_rn(b[i], __dmul_rn(s, A[i * 5 + j]));
-        A[j * 5 + j] = alpha;  // R diagonal; the sub-diagonal of column j is no longer needed
+        if (lane == 0) A[j * 5 + j] = alpha;  // R diagonal
+        __syncwarp();
     }
+    if (lane != 0) return;
     double coef[5];
     for (int j = 4; j >= 0; --j) {
         double acc = b[j];
@@ -221,6 +237,7 @@ __global__ void __launch_bounds__(256)
 k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
        const int32_t* __restrict__ pid, double2* __restrict__ local, double2* __restrict__ partial,
        int* __restrict__ err) {
+    pdl_begin();
     const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep& rep = reps[r];
     const int m = rep.m;
@@ -352,6 +369,7 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
 // Sum the block partials of each replica in a fixed order; Psi_6 = sum / N.
 __global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_total,
                               const double2* __restrict__ partial, double* __restrict__ res) {
+    pdl_begin();
     const int r = blockIdx.x;
     const Rep& rep = reps[r];
     const int b0 = rep.blk_cell;
@@ -382,47 +400,37 @@ __global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_to
 // Launchers
 // ---------------------------------------------------------------------------
 template <bool FIX, int CAP>
-static void hist_t(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
-    k_hist<FIX, CAP><<<c.blocks_cell, c.threads, size_t(h.K) * sizeof(unsigned int), c.stream>>>(
-        c.reps, c.R, h.K, h.edges, h.edgesF, cells.cnt, (const P2<FIX>*)cells.pos, cells.pid, hist);
+static cudaError_t hist_t(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
+    return launch_k(k_hist<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), size_t(h.K) * sizeof(unsigned int),
+                    c.stream, c.reps, c.R, h.K, h.edges, h.edgesF, (const uint8_t*)cells.cnt,
+                    (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid, hist);
 }
 
 cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
-    if (c.fixed) {
-        if (c.cap == 4) hist_t<true, 4>(c, h, cells, hist);
-        else hist_t<true, 9>(c, h, cells, hist);
-    } else {
-        if (c.cap == 4) hist_t<false, 4>(c, h, cells, hist);
-        else hist_t<false, 9>(c, h, cells, hist);
-    }
-    return cudaGetLastError();
+    if (c.fixed) return c.cap == 4 ? hist_t<true, 4>(c, h, cells, hist) : hist_t<true, 9>(c, h, cells, hist);
+    return c.cap == 4 ? hist_t<false, 4>(c, h, cells, hist) : hist_t<false, 9>(c, h, cells, hist);
 }
 
 cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res) {
     if (K > kMaxFitBins) return cudaErrorInvalidValue;
-    k_fit<<<c.R, 32, 0, c.stream>>>(c.reps, K, hist, res);
-    return cudaGetLastError();
+    return launch_k(k_fit, dim3(c.R), dim3(32), 0, c.stream, c.reps, K, hist, res);
 }
 
 template <bool FIX, int CAP>
-static void psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
-    k_psi6<FIX, CAP><<<c.blocks_cell, c.threads, 0, c.stream>>>(c.reps, c.R, cells.cnt, (const P2<FIX>*)cells.pos,
-                                                                  cells.pid, local, partial, err);
+static cudaError_t psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
+    return launch_k(k_psi6<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), 0, c.stream, c.reps, c.R,
+                    (const uint8_t*)cells.cnt, (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid, local, partial,
+                    err);
 }
 
 cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
-    if (c.fixed) {
-        if (c.cap == 4) psi6_t<true, 4>(c, cells, local, partial, err);
-        else psi6_t<true, 9>(c, cells, local, partial, err);
-    } else {
-        if (c.cap == 4) psi6_t<false, 4>(c, cells, local, partial, err);
-        else psi6_t<false, 9>(c, cells, local, partial, err);
-    }
-    return cudaGetLastError();
+    if (c.fixed) return c.cap == 4 ? psi6_t<true, 4>(c, cells, local, partial, err) : psi6_t<true, 9>(c, cells, local, partial, err);
+    return c.cap == 4 ? psi6_t<false, 4>(c, cells, local, partial, err) : psi6_t<false, 9>(c, cells, local, partial, err);
 }
 
 __global__ void k_record(int R, const double* __restrict__ fit, const double* __restrict__ psi,
                          double* __restrict__ series, int64_t* __restrict__ len, int64_t cap, int* __restrict__ err) {
+    pdl_begin();
     const int64_t idx = *len;
     const int r = threadIdx.x;
     if (r < R && idx < cap) {
@@ -441,13 +449,11 @@ __global__ void k_record(int R, const double* __restrict__ fit, const double* __
 
 cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* psi, double* series, int64_t* len,
                           int64_t cap, int* err) {
-    k_record<<<1, ((c.R + 31) / 32) * 32, 0, c.stream>>>(c.R, fit, psi, series, len, cap, err);
-    return cudaGetLastError();
+    return launch_k(k_record, dim3(1), dim3(((c.R + 31) / 32) * 32), 0, c.stream, c.R, fit, psi, series, len, cap, err);
 }
 
 cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res) {
-    k_psi6_reduce<<<c.R, 256, 0, c.stream>>>(c.reps, c.R, c.blocks_cell, partial, res);
-    return cudaGetLastError();
+    return launch_k(k_psi6_reduce, dim3(c.R), dim3(256), 0, c.stream, c.reps, c.R, c.blocks_cell, partial, res);
 }
 
 }  // namespace hd

@@ -22,6 +22,7 @@ namespace hd {
 
 __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__ table,
                         Frame* __restrict__ cur, uint64_t* __restrict__ sweep_ctr, int nchunk) {
+    pdl_begin();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const Rep rep = reps[r];
@@ -77,6 +78,7 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
           uint8_t* __restrict__ cnt_o, const P2<FIX>* __restrict__ pos_o, const int32_t* __restrict__ pid_o,
           uint8_t* __restrict__ cnt_n, P2<FIX>* __restrict__ pos_n, int32_t* __restrict__ pid_n,
           int* __restrict__ err) {
+    pdl_begin();
     const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
     const int m = rep.m;
@@ -127,6 +129,7 @@ template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int j, int p,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
+    pdl_begin();
     constexpr bool kAllCells = FIX;
     const int r = find_rep<kGridAct>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
@@ -216,6 +219,7 @@ template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_positions(const Rep* __restrict__ reps, int R, const Frame* __restrict__ cur, const uint8_t* __restrict__ cnt,
             const P2<FIX>* __restrict__ pos, const int32_t* __restrict__ pid, double* __restrict__ xy) {
+    pdl_begin();
     const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
     const int m = rep.m;
@@ -252,61 +256,42 @@ k_positions(const Rep* __restrict__ reps, int R, const Frame* __restrict__ cur, 
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t* sweep_ctr, int nchunk) {
-    k_draws<<<(c.R + 63) / 64, 64, 0, c.stream>>>(c.reps, c.R, table, cur, sweep_ctr, nchunk);
-    return cudaGetLastError();
+    return launch_k(k_draws, dim3((c.R + 63) / 64), dim3(64), 0, c.stream, c.reps, c.R, table, cur, sweep_ctr, nchunk);
 }
 
 template <bool FIX, int CAP>
-static void rebuild_t(const LaunchCfg& c, const Frame* table, int j, CellBufs a, CellBufs b, int* err) {
-    k_rebuild<FIX, CAP><<<c.blocks_cell, c.threads, 0, c.stream>>>(
-        c.reps, c.R, table, j, a.cnt, (const P2<FIX>*)a.pos, a.pid, b.cnt, (P2<FIX>*)b.pos, b.pid, err);
+static cudaError_t rebuild_t(const LaunchCfg& c, const Frame* table, int j, CellBufs a, CellBufs b, int* err) {
+    return launch_k(k_rebuild<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), 0, c.stream, c.reps, c.R, table, j,
+                    a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt, (P2<FIX>*)b.pos, b.pid, err);
 }
 
 cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to, int* err) {
-    if (c.fixed) {
-        if (c.cap == 4) rebuild_t<true, 4>(c, table, j, from, to, err);
-        else rebuild_t<true, 9>(c, table, j, from, to, err);
-    } else {
-        if (c.cap == 4) rebuild_t<false, 4>(c, table, j, from, to, err);
-        else rebuild_t<false, 9>(c, table, j, from, to, err);
-    }
-    return cudaGetLastError();
+    if (c.fixed) return c.cap == 4 ? rebuild_t<true, 4>(c, table, j, from, to, err) : rebuild_t<true, 9>(c, table, j, from, to, err);
+    return c.cap == 4 ? rebuild_t<false, 4>(c, table, j, from, to, err) : rebuild_t<false, 9>(c, table, j, from, to, err);
 }
 
 template <bool FIX, int CAP>
-static void pass_t(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
-                   unsigned long long* counters) {
-    k_pass<FIX, CAP><<<c.blocks_act, c.threads, 0, c.stream>>>(c.reps, c.R, table, j, p, cells.cnt,
-                                                                 (P2<FIX>*)cells.pos, cells.pid, counters);
+static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
+                          unsigned long long* counters) {
+    return launch_k(k_pass<FIX, CAP>, dim3(c.blocks_act), dim3(c.threads), 0, c.stream, c.reps, c.R, table, j, p,
+                    (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
 }
 
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters) {
-    if (c.fixed) {
-        if (c.cap == 4) pass_t<true, 4>(c, table, j, p, cells, counters);
-        else pass_t<true, 9>(c, table, j, p, cells, counters);
-    } else {
-        if (c.cap == 4) pass_t<false, 4>(c, table, j, p, cells, counters);
-        else pass_t<false, 9>(c, table, j, p, cells, counters);
-    }
-    return cudaGetLastError();
+    if (c.fixed) return c.cap == 4 ? pass_t<true, 4>(c, table, j, p, cells, counters) : pass_t<true, 9>(c, table, j, p, cells, counters);
+    return c.cap == 4 ? pass_t<false, 4>(c, table, j, p, cells, counters) : pass_t<false, 9>(c, table, j, p, cells, counters);
 }
 
 template <bool FIX, int CAP>
-static void positions_t(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy) {
-    k_positions<FIX, CAP><<<c.blocks_cell, c.threads, 0, c.stream>>>(c.reps, c.R, cur, cells.cnt,
-                                                                       (const P2<FIX>*)cells.pos, cells.pid, xy);
+static cudaError_t positions_t(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy) {
+    return launch_k(k_positions<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), 0, c.stream, c.reps, c.R, cur,
+                    (const uint8_t*)cells.cnt, (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid, xy);
 }
 
 cudaError_t launch_positions(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy) {
-    if (c.fixed) {
-        if (c.cap == 4) positions_t<true, 4>(c, cur, cells, xy);
-        else positions_t<true, 9>(c, cur, cells, xy);
-    } else {
-        if (c.cap == 4) positions_t<false, 4>(c, cur, cells, xy);
-        else positions_t<false, 9>(c, cur, cells, xy);
-    }
-    return cudaGetLastError();
+    if (c.fixed) return c.cap == 4 ? positions_t<true, 4>(c, cur, cells, xy) : positions_t<true, 9>(c, cur, cells, xy);
+    return c.cap == 4 ? positions_t<false, 4>(c, cur, cells, xy) : positions_t<false, 9>(c, cur, cells, xy);
 }
 
 }  // namespace hd
