@@ -379,7 +379,8 @@ def run_reference(args):
         return
     t0 = time.perf_counter()
     per = []
-    total_budget = max(2.0, 30.0 / max(1, args.steps + args.warmup))
+    # each step is a bounded sample; the whole run takes about 3 x --cpu-seconds
+    total_budget = max(1.0, 3.0 * args.cpu_seconds / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
         r = cpu_oracle(args, args.form, total_budget)
         if k >= args.warmup:

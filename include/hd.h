@@ -212,6 +212,37 @@ hd_status hd_series(hd_ctx *ctx, int64_t *n_steps, double *out, int64_t max_step
 hd_status hd_series_clear(hd_ctx *ctx);
 
 /*
+ * Checkpoint and resume of long runs (the paper's production runs span
+ * 10^11 - 10^13 displacements, Table I).  The chain state is the cell frame
+ * (occupancy, offsets and ids in slot order), the current frame shift, the
+ * sweep counters and the trial counters; with the counter-based generator a
+ * restored context continues the chain bit-exactly.
+ *   hd_checkpoint_size  *bytes receives the size of the checkpoint.
+ *   hd_checkpoint       writes it to a caller-owned host buffer of at least
+ *                       that size; synchronises.
+ *   hd_restore          loads a checkpoint into a context created with the
+ *                       same N, eta, sigma, delta, seed and options
+ *                       (HD_ERR_ARG if the header does not match); the
+ *                       measurement series is kept.  Synchronises.
+ */
+hd_status hd_checkpoint_size(hd_ctx *ctx, size_t *bytes);
+
+/*
+ * Maximum trial displacement per replica.  hd_set_delta sets delta[R] (sigma
+ * units; 0 < delta < cell side, and at least one 2^-24 sigma step in the
+ * fixed form).  hd_tune_delta runs `probes` bursts of `sweeps_per_probe`
+ * sweeps, measuring each replica's acceptance and scaling its delta by
+ * (acceptance/target)^0.7 (clamped to a factor 1/4..4 and to the valid range)
+ * toward `target` in (0, 1); the chains advance during tuning and
+ * delta is frozen afterwards, so production sweeps keep detailed balance.
+ * delta_out[R] (nullable) receives the tuned values.  Synchronises.
+ */
+hd_status hd_set_delta(hd_ctx *ctx, const double *delta);
+hd_status hd_tune_delta(hd_ctx *ctx, double target, int32_t sweeps_per_probe, int32_t probes, double *delta_out);
+hd_status hd_checkpoint(hd_ctx *ctx, void *buf, size_t bytes);
+hd_status hd_restore(hd_ctx *ctx, const void *buf, size_t bytes);
+
+/*
  * Global Psi_6 = (1/N) sum_j psi_j from a per-disk field that the caller
  * already holds on the device (for instance the local field of hd_psi6,
  * copied to device memory), for callers that may not allocate device memory

@@ -857,6 +857,212 @@ hd_status hd_series_clear(hd_ctx* ctx) {
     return HD_OK;
 }
 
+// Checkpoint layout: header, per-replica geometry keys, then the current cell
+// generation (occupancy, slot planes of offsets, slot planes of ids), frames,
+// sweep counters, trial counters and host sweep tallies.
+namespace {
+struct CkHeader {
+    char magic[8];
+    int32_t version, R, fixed, cap;
+    int64_t Ctot, Ntot;
+    int32_t K, sweep_kernel;
+};
+struct CkRep {
+    int64_t N;
+    int32_t m, W, D, nt;
+    uint32_t key0, key1;
+    double w, delta, dr;
+};
+constexpr char kCkMagic[8] = {'H', 'D', 'C', 'K', 'P', 'T', '0', '1'};
+
+size_t pos_bytes(const hd_ctx* ctx) { return ctx->fixed ? sizeof(int2) : sizeof(double2); }
+
+size_t checkpoint_bytes(const hd_ctx* ctx) {
+    const size_t slots = size_t(ctx->Ctot) * ctx->cap;
+    return sizeof(CkHeader) + sizeof(CkRep) * size_t(ctx->R) + size_t(ctx->Ctot) + slots * pos_bytes(ctx) +
+           slots * sizeof(int32_t) + sizeof(Frame) * size_t(ctx->R) + sizeof(uint64_t) * size_t(ctx->R) +
+           sizeof(unsigned long long) * 2 * size_t(ctx->R) + sizeof(int64_t) * size_t(ctx->R);
+}
+
+void fill_header(const hd_ctx* ctx, CkHeader& h, std::vector<CkRep>& reps) {
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkMagic, sizeof(kCkMagic));
+    h.version = 1;
+    h.R = ctx->R;
+    h.fixed = ctx->fixed ? 1 : 0;
+    h.cap = ctx->cap;
+    h.Ctot = ctx->Ctot;
+    h.Ntot = ctx->Ntot;
+    h.K = ctx->K;
+    h.sweep_kernel = ctx->fused ? 1 : 0;
+    reps.assign(size_t(ctx->R), CkRep{});
+    for (int r = 0; r < ctx->R; ++r) {
+        const Rep& s = ctx->reps[size_t(r)];
+        CkRep& c = reps[size_t(r)];
+        std::memset(&c, 0, sizeof(c));
+        c.N = s.N;
+        c.m = s.m;
+        c.W = s.W;
+        c.D = s.D;
+        c.nt = s.nt;
+        c.key0 = s.key0;
+        c.key1 = s.key1;
+        c.w = s.w;
+        c.delta = s.delta;
+        c.dr = s.dr;
+    }
+}
+}  // namespace
+
+namespace {
+// Set replica r's step to delta (sigma units) in the host copy; false if the
+// value is out of range for the cell.
+bool set_rep_delta(hd_ctx* ctx, int r, double delta) {
+    Rep& rep = ctx->reps[size_t(r)];
+    if (!(delta > 0.0)) return false;
+    if (ctx->fixed) {
+        const int64_t D = std::llround(delta * kFx);
+        if (D < 1 || D >= rep.W) return false;
+        rep.D = int32_t(D);
+        rep.delta = delta;
+    } else {
+        if (!(delta < rep.w)) return false;
+        rep.delta = delta;
+    }
+    return true;
+}
+
+hd_status upload_reps(hd_ctx* ctx) {
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    HD_CK(ctx, cudaMemcpy(ctx->reps_d, ctx->reps.data(), sizeof(Rep) * size_t(ctx->R), cudaMemcpyHostToDevice));
+    return HD_OK;
+}
+}  // namespace
+
+hd_status hd_set_delta(hd_ctx* ctx, const double* delta) {
+    if (!ctx || !delta) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const std::vector<Rep> saved = ctx->reps;
+    for (int r = 0; r < ctx->R; ++r) {
+        if (!set_rep_delta(ctx, r, delta[r] / ctx->sigma)) {
+            ctx->reps = saved;
+            return HD_ERR_ARG;
+        }
+    }
+    return upload_reps(ctx);
+}
+
+hd_status hd_tune_delta(hd_ctx* ctx, double target, int32_t sweeps_per_probe, int32_t probes, double* delta_out) {
+    if (!ctx || !(target > 0.0 && target < 1.0) || sweeps_per_probe < 1 || probes < 1) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const int R = ctx->R;
+    std::vector<double> lo(size_t(R), 0.0), hi(size_t(R), 0.0);
+    std::vector<unsigned long long> c0(size_t(2 * R)), c1(size_t(2 * R));
+    for (int r = 0; r < R; ++r) {
+        const Rep& rep = ctx->reps[size_t(r)];
+        lo[size_t(r)] = ctx->fixed ? 1.0 / kFx : 1e-6;
+        hi[size_t(r)] = ctx->fixed ? double(rep.W - 1) / kFx : rep.w_below;
+    }
+    // Damped multiplicative update on log(delta): the acceptance falls
+    // smoothly with delta, so log(delta) <- log(delta) + g*log(acc/target)
+    // converges for any local log-log slope below 2/g, and it keeps tracking
+    // a chain whose acceptance still drifts (e.g. relaxing from a lattice),
+    // which an interval bisection cannot.
+    const double g = 0.7;
+    for (int it = 0; it < probes; ++it) {
+        HD_CK(ctx, cudaMemcpy(c0.data(), ctx->counters, sizeof(unsigned long long) * c0.size(), cudaMemcpyDeviceToHost));
+        const hd_status s = hd_sweep(ctx, sweeps_per_probe);
+        if (s != HD_OK) return s;
+        HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+        HD_CK(ctx, cudaMemcpy(c1.data(), ctx->counters, sizeof(unsigned long long) * c1.size(), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < R; ++r) {
+            const double att = double(c1[size_t(2 * r)] - c0[size_t(2 * r)]);
+            const double acc = double(c1[size_t(2 * r + 1)] - c0[size_t(2 * r + 1)]);
+            if (att <= 0.0) continue;
+            const double d = ctx->reps[size_t(r)].delta;
+            const double f = acc > 0.0 ? std::pow(acc / att / target, g) : 0.25;
+            const double next = std::min(hi[size_t(r)], std::max(lo[size_t(r)], d * std::min(4.0, std::max(0.25, f))));
+            set_rep_delta(ctx, r, next);
+        }
+        const hd_status u = upload_reps(ctx);
+        if (u != HD_OK) return u;
+    }
+    if (delta_out)
+        for (int r = 0; r < R; ++r) delta_out[r] = ctx->reps[size_t(r)].delta * ctx->sigma;
+    return check_flags(ctx);
+}
+
+hd_status hd_checkpoint_size(hd_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return HD_ERR_ARG;
+    *bytes = checkpoint_bytes(ctx);
+    return HD_OK;
+}
+
+hd_status hd_checkpoint(hd_ctx* ctx, void* buf, size_t bytes) {
+    if (!ctx || !buf || bytes < checkpoint_bytes(ctx)) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const hd_status f = check_flags(ctx);
+    if (f != HD_OK) return f;
+    CkHeader h;
+    std::vector<CkRep> reps;
+    fill_header(ctx, h, reps);
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    std::memcpy(p, reps.data(), sizeof(CkRep) * reps.size());
+    p += sizeof(CkRep) * reps.size();
+    const size_t slots = size_t(ctx->Ctot) * ctx->cap;
+    const CellBufs& b = ctx->buf[ctx->cur];
+    HD_CK(ctx, cudaMemcpy(p, b.cnt, size_t(ctx->Ctot), cudaMemcpyDeviceToHost));
+    p += size_t(ctx->Ctot);
+    HD_CK(ctx, cudaMemcpy(p, b.pos, slots * pos_bytes(ctx), cudaMemcpyDeviceToHost));
+    p += slots * pos_bytes(ctx);
+    HD_CK(ctx, cudaMemcpy(p, b.pid, slots * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    p += slots * sizeof(int32_t);
+    HD_CK(ctx, cudaMemcpy(p, ctx->frame, sizeof(Frame) * size_t(ctx->R), cudaMemcpyDeviceToHost));
+    p += sizeof(Frame) * size_t(ctx->R);
+    HD_CK(ctx, cudaMemcpy(p, ctx->sweep_ctr, sizeof(uint64_t) * size_t(ctx->R), cudaMemcpyDeviceToHost));
+    p += sizeof(uint64_t) * size_t(ctx->R);
+    HD_CK(ctx, cudaMemcpy(p, ctx->counters, sizeof(unsigned long long) * 2 * size_t(ctx->R), cudaMemcpyDeviceToHost));
+    p += sizeof(unsigned long long) * 2 * size_t(ctx->R);
+    std::memcpy(p, ctx->sweeps.data(), sizeof(int64_t) * size_t(ctx->R));
+    return HD_OK;
+}
+
+hd_status hd_restore(hd_ctx* ctx, const void* buf, size_t bytes) {
+    if (!ctx || !buf || bytes < checkpoint_bytes(ctx)) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    CkHeader want, got;
+    std::vector<CkRep> want_reps;
+    fill_header(ctx, want, want_reps);
+    const unsigned char* p = static_cast<const unsigned char*>(buf);
+    std::memcpy(&got, p, sizeof(got));
+    p += sizeof(got);
+    if (std::memcmp(&got, &want, sizeof(got)) != 0) return HD_ERR_ARG;
+    if (std::memcmp(p, want_reps.data(), sizeof(CkRep) * want_reps.size()) != 0) return HD_ERR_ARG;
+    p += sizeof(CkRep) * want_reps.size();
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const size_t slots = size_t(ctx->Ctot) * ctx->cap;
+    const CellBufs& b = ctx->buf[ctx->cur];
+    HD_CK(ctx, cudaMemcpy(b.cnt, p, size_t(ctx->Ctot), cudaMemcpyHostToDevice));
+    p += size_t(ctx->Ctot);
+    HD_CK(ctx, cudaMemcpy(b.pos, p, slots * pos_bytes(ctx), cudaMemcpyHostToDevice));
+    p += slots * pos_bytes(ctx);
+    HD_CK(ctx, cudaMemcpy(b.pid, p, slots * sizeof(int32_t), cudaMemcpyHostToDevice));
+    p += slots * sizeof(int32_t);
+    // the other generation's occupancy must be zero for the next scatter rebuild
+    HD_CK(ctx, cudaMemset(ctx->buf[ctx->cur ^ 1].cnt, 0, size_t(ctx->Ctot) + 4));
+    HD_CK(ctx, cudaMemcpy(ctx->frame, p, sizeof(Frame) * size_t(ctx->R), cudaMemcpyHostToDevice));
+    p += sizeof(Frame) * size_t(ctx->R);
+    HD_CK(ctx, cudaMemcpy(ctx->sweep_ctr, p, sizeof(uint64_t) * size_t(ctx->R), cudaMemcpyHostToDevice));
+    p += sizeof(uint64_t) * size_t(ctx->R);
+    HD_CK(ctx, cudaMemcpy(ctx->counters, p, sizeof(unsigned long long) * 2 * size_t(ctx->R), cudaMemcpyHostToDevice));
+    p += sizeof(unsigned long long) * 2 * size_t(ctx->R);
+    std::memcpy(ctx->sweeps.data(), p, sizeof(int64_t) * size_t(ctx->R));
+    return HD_OK;
+}
+
 hd_status hd_profile(hd_ctx* ctx, int32_t enable) {
     if (!ctx) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;

@@ -1,8 +1,8 @@
 // hd_cell.cuh -- per-cell steps of the checkerboard sweep (Engel et al.,
 // arXiv:1211.1645, Sec. II.B), shared by the split kernels (one launch per
 // rebuild and per colour pass) and the fused kernel (one launch per sweep):
-//   gather_cell  builds one cell of the new shifted frame from the 2 x 2 old
-//                cells that can feed it, occupants ordered by ascending id;
+//   sort_by_id   orders a cell's occupants by id (the shuffle's base order);
+//   claim_slot   claims a slot of a destination cell during the rebuild;
 //   try_cell     shuffles one active cell's occupants and makes its serial
 //                trial moves against the cell itself and its neighbours.
 #pragma once
@@ -25,22 +25,21 @@ constexpr int kEagerSlots = 2;
 // in registers; a higher slot is fetched when a (rare) crowded cell needs it.
 template <bool FIX, bool IDS>
 struct CellRegs {
-    const P2<FIX>* pos;   // slot 0 of this cell; slot k at pos[k * stride]
-    const int32_t* pid;
+    uint32_t c;           // cell index; slot k of the cell is entry k * stride + c
     P2<FIX> s[kEagerSlots];
     int32_t id[IDS ? kEagerSlots : 1];
     int n;
 
-    __device__ __forceinline__ P2<FIX> slot(int k, uint32_t stride) const {
+    __device__ __forceinline__ P2<FIX> slot(int k, const P2<FIX>* __restrict__ pos, uint32_t stride) const {
         if (k == 0) return s[0];
         if (k == 1) return s[1];
-        return __ldg(pos + size_t(k) * stride);
+        return __ldg(pos + size_t(k) * stride + c);
     }
-    __device__ __forceinline__ int32_t slot_id(int k, uint32_t stride) const {
+    __device__ __forceinline__ int32_t slot_id(int k, const int32_t* __restrict__ pid, uint32_t stride) const {
         if constexpr (IDS) {
             if (k == 0) return id[0];
             if (k == 1) return id[1];
-            return __ldg(pid + size_t(k) * stride);
+            return __ldg(pid + size_t(k) * stride + c);
         }
         return 0;
     }
@@ -59,8 +58,7 @@ __device__ __forceinline__ void load_cell(const uint8_t* __restrict__ cnt, const
                                           const int32_t* __restrict__ pid, uint32_t stride, uint32_t c,
                                           CellRegs<FIX, IDS>& out) {
     out.n = occupancy<CAP>(cnt, c);
-    out.pos = pos + c;
-    out.pid = IDS ? pid + c : nullptr;
+    out.c = c;
 #pragma unroll
     for (int k = 0; k < kEagerSlots; ++k) {
         out.s[k] = __ldg(pos + size_t(k) * stride + c);
@@ -111,66 +109,6 @@ __device__ __forceinline__ void cswap(NewCell<FIX, CAP>& c, int a, int b) {
         const P2<FIX> u = c.p[a];
         c.p[a] = c.p[b];
         c.p[b] = u;
-    }
-}
-
-// Build new cell (cx, cy) from its four feeding old cells src[b] at (ocx[b],
-// ocy[b]): every occupant is moved into the new frame by the same per-disk
-// frame change (frame_change_fp64 / frame_change_fixed); those that land in
-// (cx, cy) are kept, then ordered by id with a sorting network.
-template <bool FIX, int CAP>
-__device__ __forceinline__ void gather_cell(const Rep& rep, const ShiftDelta<FIX>& sd,
-                                            const CellRegs<FIX, true> (&src)[4], const int (&ocx)[4],
-                                            const int (&ocy)[4], int cx, int cy, NewCell<FIX, CAP>& out) {
-    out.n = 0;
-    out.over = false;
-#pragma unroll
-    for (int q = 0; q < CAP; ++q) {
-        out.id[q] = INT_MAX;
-        out.p[q] = P2<FIX>{};
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int nb = src[b].n;
-        for (int k = 0; k < nb; ++k) {
-            const P2<FIX> q = src[b].slot(k, rep.stride32);
-            int tcx, tcy;
-            P2<FIX> nq;
-            if constexpr (FIX) {
-                frame_change_fixed(sd.fx, rep.W, rep.m, ocx[b], q.x, tcx, nq.x);
-                frame_change_fixed(sd.fy, rep.W, rep.m, ocy[b], q.y, tcy, nq.y);
-            } else {
-                frame_change_fp64(sd.dx, rep.w, rep.w_below, rep.m, ocx[b], q.x, tcx, nq.x);
-                frame_change_fp64(sd.dy, rep.w, rep.w_below, rep.m, ocy[b], q.y, tcy, nq.y);
-            }
-            if (tcx != cx || tcy != cy) continue;
-            const int32_t id = src[b].slot_id(k, rep.stride32);
-            if (out.n >= CAP) {
-                out.over = true;
-                continue;
-            }
-#pragma unroll
-            for (int s = 0; s < CAP; ++s)
-                if (s == out.n) {
-                    out.id[s] = id;
-                    out.p[s] = nq;
-                }
-            ++out.n;
-        }
-    }
-    if (out.n > 1) {
-        if constexpr (CAP == 4) {
-            cswap(out, 0, 1);
-            cswap(out, 2, 3);
-            cswap(out, 0, 2);
-            cswap(out, 1, 3);
-            cswap(out, 1, 2);
-        } else {
-#pragma unroll
-            for (int i = 1; i < CAP; ++i)
-#pragma unroll
-                for (int s = i; s > 0; --s) cswap(out, s - 1, s);
-        }
     }
 }
 

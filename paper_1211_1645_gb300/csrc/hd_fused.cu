@@ -104,7 +104,7 @@ k_sweep_fused(const Rep* __restrict__ reps, int R, const Frame* __restrict__ tab
         CellRegs<FIX, true> src;
         load_cell<FIX, true, CAP>(cnt_o, pos_o, pid_o, rep.stride32, oc, src);
         for (int k = 0; k < n; ++k) {
-            const P2<FIX> q = src.slot(k, rep.stride32);
+            const P2<FIX> q = src.slot(k, pos_o, rep.stride32);
             int tcx, tcy;
             P2<FIX> nq;
             if constexpr (FIX) {
@@ -120,7 +120,7 @@ k_sweep_fused(const Rep* __restrict__ reps, int R, const Frame* __restrict__ tab
             const int s = claim_slot(s_cnt, uint32_t(pl2));
             if (s < CAP) {
                 s_pos[s * F::NC + pl2] = nq;
-                s_pid[s * F::NC + pl2] = src.slot_id(k, rep.stride32);
+                s_pid[s * F::NC + pl2] = src.slot_id(k, pid_o, rep.stride32);
             } else {
                 over = true;
             }

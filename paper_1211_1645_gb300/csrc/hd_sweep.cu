@@ -95,8 +95,8 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
     load_cell<FIX, true, CAP>(cnt_o, pos_o, pid_o, rep.stride32, c, src);
     bool over = false;
     for (int k = 0; k < n; ++k) {
-        const P2<FIX> q = src.slot(k, rep.stride32);
-        const int32_t id = src.slot_id(k, rep.stride32);
+        const P2<FIX> q = src.slot(k, pos_o, rep.stride32);
+        const int32_t id = src.slot_id(k, pid_o, rep.stride32);
         int tcx, tcy;
         P2<FIX> nq;
         if constexpr (FIX) {
@@ -166,8 +166,8 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
 #pragma unroll
             for (int q = 0; q < CAP; ++q) {
                 const bool live = q < kEagerSlots || q < n;
-                P[q] = live ? own.slot(q, rep.stride32) : P2<FIX>{};
-                ids[q] = live ? own.slot_id(q, rep.stride32) : 0;
+                P[q] = live ? own.slot(q, pos, rep.stride32) : P2<FIX>{};
+                ids[q] = live ? own.slot_id(q, pid, rep.stride32) : 0;
             }
             if (n > 1) sort_by_id<FIX, CAP>(P, ids, n);
             auto neighbours_clear = [&](const P2<FIX>& np) {
@@ -181,7 +181,7 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                         for (int k = 0; k < kEagerSlots; ++k)
                             if (k < nb[i].n) ok = ok && pair_clear<FIX>(nb[i].s[k], ox, oy, np, rep);
                         for (int k = kEagerSlots; k < nb[i].n; ++k)
-                            ok = ok && pair_clear<FIX>(nb[i].slot(k, rep.stride32), ox, oy, np, rep);
+                            ok = ok && pair_clear<FIX>(nb[i].slot(k, pos, rep.stride32), ox, oy, np, rep);
                     }
                 } else {
                     for (int i = 0; i < 9 && ok; ++i) {
@@ -189,7 +189,7 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                         const int ox = i % 3 - 1, oy = i / 3 - 1;
                         CellRegs<FIX, false> c;
                         load_cell<FIX, false, CAP>(cnt, pos, nullptr, rep.stride32, yp[i / 3] + xp[i % 3], c);
-                        for (int k = 0; k < c.n && ok; ++k) ok = pair_clear<FIX>(c.slot(k, rep.stride32), ox, oy, np, rep);
+                        for (int k = 0; k < c.n && ok; ++k) ok = pair_clear<FIX>(c.slot(k, pos, rep.stride32), ox, oy, np, rep);
                     }
                 }
                 return ok;

@@ -103,6 +103,11 @@ def load(path: str | None = None):
             "hd_series": (S, [P, P, P, c.c_int64]),
             "hd_series_clear": (S, [P]),
             "hd_psi6_mean_noalloc": (S, [P, c.c_int64, P, P]),
+            "hd_checkpoint_size": (S, [P, c.POINTER(c.c_size_t)]),
+            "hd_set_delta": (S, [P, P]),
+            "hd_tune_delta": (S, [P, c.c_double, c.c_int32, c.c_int32, P]),
+            "hd_checkpoint": (S, [P, P, c.c_size_t]),
+            "hd_restore": (S, [P, P, c.c_size_t]),
             "hd_kernel_times": (S, [P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -262,6 +267,31 @@ def hd_series(h, max_steps: int = 1 << 20):
     return out[: int(n[0])]
 
 
+def hd_checkpoint(h) -> bytes:
+    """The full chain state as bytes (restore with hd_restore)."""
+    n = ctypes.c_size_t(0)
+    _check(load().hd_checkpoint_size(h, ctypes.byref(n)), "hd_checkpoint_size")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().hd_checkpoint(h, buf, n.value), "hd_checkpoint")
+    return buf.raw
+
+
+def hd_restore(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().hd_restore(h, buf, len(blob)), "hd_restore")
+
+
+def hd_set_delta(h, delta):
+    d = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, np.float64), (hd_replicas(h),)))
+    _check(load().hd_set_delta(h, _ptr(d)), "hd_set_delta")
+
+
+def hd_tune_delta(h, target: float = 0.3, sweeps_per_probe: int = 20, probes: int = 10) -> np.ndarray:
+    out = np.zeros(hd_replicas(h), np.float64)
+    _check(load().hd_tune_delta(h, float(target), int(sweeps_per_probe), int(probes), _ptr(out)), "hd_tune_delta")
+    return out
+
+
 def hd_series_clear(h):
     _check(load().hd_series_clear(h), "hd_series_clear")
 
@@ -335,6 +365,18 @@ class HardDisks:
 
     def series(self):
         return hd_series(self.h)
+
+    def set_delta(self, delta):
+        hd_set_delta(self.h, delta)
+
+    def tune_delta(self, target=0.3, sweeps_per_probe=20, probes=10):
+        return hd_tune_delta(self.h, target, sweeps_per_probe, probes)
+
+    def checkpoint(self):
+        return hd_checkpoint(self.h)
+
+    def restore(self, blob):
+        hd_restore(self.h, blob)
 
     def series_reserve(self, steps):
         hd_series_reserve(self.h, steps)

@@ -1,0 +1,85 @@
+"""Host-side logic of bench.py without a GPU: the multi-rank reduction used
+under torchrun (world size 2, gloo, on CPU), the reference arm (the CPU
+oracle) and the JSON contract of its line."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+WORKER = r'''
+import os, sys, json
+sys.path.insert(0, os.environ["ROOT"])
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo", init_method="env://")
+rank, world = dist.get_rank(), dist.get_world_size()
+bench.barrier(world)
+tmax, tsum = bench.reduce_max_sum(world, 10.0 * (rank + 1), 100.0 + rank, "cpu")
+print(json.dumps({"rank": rank, "tmax": tmax, "tsum": tsum}), flush=True)
+dist.destroy_process_group()
+'''
+
+
+def test_two_rank_reduction_gloo(tmp_path):
+    """Max of the step time and sum of the attempts over ranks, as rank 0
+    reports them for weak scaling over independent replicas."""
+    script = tmp_path / "worker.py"
+    script.write_text(WORKER)
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, ROOT=ROOT, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                   WORLD_SIZE="2", LOCAL_RANK=str(rank))
+        procs.append(subprocess.Popen([sys.executable, str(script)], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=180) for p in procs]
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e
+    res = [json.loads(o.strip().splitlines()[-1]) for o, _ in outs]
+    for r in res:
+        assert r["tmax"] == 20.0 and r["tsum"] == 201.0
+
+
+def test_reference_arm_prints_contract_line():
+    """--impl reference times the CPU oracle on a bounded sample and prints
+    one JSON line with impl, cpu_baseline and e2e."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "4096",
+                          "--eta", "0.7", "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5"], capture_output=True, text=True,
+                         timeout=300, env=dict(os.environ, RANK="0"))
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["unit"] == "trial moves/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["higher_is_better"] is True
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "1024",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=120,
+                         env=dict(os.environ, RANK="1"))
+    assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_algorithmic_bytes():
+    sys.path.insert(0, ROOT)
+    import bench
+    N, m = 1 << 20, 1072
+    assert bench.algorithmic_bytes("sweep", N, m, "fixed") == 2 * (N * 12 + m * m)
+    assert bench.algorithmic_bytes("pass", N, m, "fixed") == m * m + N * 8 + (N // 4) * 8
+    assert bench.algorithmic_bytes("pass", N, m, "fp64") == m * m + N * 16 + (N // 4) * 16

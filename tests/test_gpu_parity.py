@@ -289,3 +289,34 @@ def test_graph_engine_batched(hd, oracle_mod, form):
     for r, o in enumerate(os_):
         assert np.array_equal(xy[off:off + Ns[r]], o.positions())
         off += Ns[r]
+
+
+@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_checkpoint_resume_bit_exact(hd, oracle_mod, form, kernel):
+    """A chain checkpointed after 40 sweeps and restored into a fresh context
+    continues exactly as the uninterrupted chain (and as the oracle)."""
+    g, o = make_pair(hd, oracle_mod, form, 1000, 0.70, 0.12, 77, kernel=kernel)
+    g.sweep(40)
+    blob = g.checkpoint()
+    g.sweep(30)
+    o.sweep(70)
+    g2 = hd.HardDisks(1000, 0.70, 0.12, 77, precision=form, sweep_kernel=kernel)
+    g2.restore(blob)
+    g2.sweep(30)
+    assert np.array_equal(g2.positions(), g.positions())
+    assert [int(x[0]) for x in g2.stats()] == [int(x[0]) for x in g.stats()]
+    assert_same_state(g2, o)
+    assert g2.geometry()["sweeps"] == 70
+
+
+def test_restore_rejects_other_geometry(hd):
+    from paper_1211_1645_gb300.hd import HD_ERR_ARG, HDError
+    g = hd.HardDisks(1000, 0.70, 0.12, 77, precision="fixed")
+    blob = g.checkpoint()
+    other = hd.HardDisks(1000, 0.70, 0.12, 78, precision="fixed")  # different seed
+    with pytest.raises(HDError) as e:
+        other.restore(blob)
+    assert e.value.status == HD_ERR_ARG
+    with pytest.raises(HDError):
+        g.restore(blob[:100])

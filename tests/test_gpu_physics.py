@@ -1,0 +1,71 @@
+"""GPU tests of the chain's statistics: step-size tuning, and agreement of
+the fixed-point and FP64 equations of state (different Markov chains of the
+same ensemble) within three combined standard errors over independent
+replicas."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_1211_1645_gb300 as hd
+    hd.load()
+    return hd
+
+
+@pytest.mark.parametrize("form,N", [("fixed", 65536), ("fp64", 16384)])
+def test_tune_delta_reaches_target_acceptance(hd, form, N):
+    """Config 2 asks for delta tuned to ~30% acceptance; after tuning the
+    acceptance of later sweeps is within 0.03 of the target."""
+    g = hd.HardDisks(N, 0.708, 0.1, 3, precision=form)
+    g.sweep(100)
+    d = g.tune_delta(0.30, sweeps_per_probe=20, probes=12)
+    assert 0.0 < d[0] < g.geometry()["w"]
+    a0, c0 = (int(x[0]) for x in g.stats())
+    g.sweep(100)
+    a1, c1 = (int(x[0]) for x in g.stats())
+    assert abs((c1 - c0) / (a1 - a0) - 0.30) < 0.03
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_set_delta_matches_oracle(hd, oracle_mod, form):
+    g = hd.HardDisks(1000, 0.65, 0.1, 5, precision=form)
+    g.set_delta(0.2)
+    o = oracle_mod.OracleChain(1000, 0.65, 0.2, 5, form=form)
+    g.sweep(25)
+    o.sweep(25)
+    assert np.array_equal(g.positions(), o.positions())
+    from paper_1211_1645_gb300.hd import HD_ERR_ARG, HDError
+    with pytest.raises(HDError) as e:
+        g.set_delta(10.0)  # beyond the cell side
+    assert e.value.status == HD_ERR_ARG
+
+
+def test_fixed_vs_fp64_equation_of_state(hd):
+    """beta P / rho at eta = 0.716, N = 64^2, eight independent replicas per
+    form (one batch each): the two forms' means agree within 3 combined
+    standard errors."""
+    R, N, eta = 8, 4096, 0.716
+    res = {}
+    for form, seed0 in (("fixed", 100), ("fp64", 200)):
+        g = hd.HardDisks([N] * R, [eta] * R, [0.1] * R, [seed0 + r for r in range(R)], precision=form)
+        g.sweep(4000)
+        g.series_reserve(64)
+        g.run(40, 100, measure=True)
+        s = g.series()[:, :, 0]  # [step, replica]
+        means = s.mean(axis=0)
+        res[form] = (means.mean(), means.std(ddof=1) / np.sqrt(R))
+        g.close()
+    (mf, sf), (md, sd) = res["fixed"], res["fp64"]
+    assert 7.0 < mf < 16.0 and 7.0 < md < 16.0  # dense liquid, still relaxing from the lattice
+    assert abs(mf - md) < 3.0 * np.hypot(sf, sd), res
+
+
+def test_autotuner_picks_a_valid_fast_configuration(hd):
+    from paper_1211_1645_gb300.tune import autotune
+    best, table = autotune(65536, 0.708, 0.1, cell_mins=(2.0, 2.4), block_threads=(128, 256), sweeps=20, steps=2)
+    assert best is not None and len(table) >= 3
+    assert best["trial_moves_per_s"] == max(r["trial_moves_per_s"] for r in table)
+    assert best["cell_min"] in (2.0, 2.4) and best["sweep_kernel"] in ("split", "fused")
