@@ -99,6 +99,7 @@ struct hd_ctx {
         c.cap = cap;
         c.fixed = fixed;
         c.threads = threads;
+        c.nt1 = std::all_of(reps.begin(), reps.end(), [](const hd::Rep& r) { return r.nt == 1; });
         c.blocks_cell = blocks_cell;
         c.blocks_act = blocks_act;
         c.blocks_tile = blocks_tile;
@@ -160,6 +161,12 @@ hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64
     r.N = N;
     r.m = m;
     r.hm = m / 2;
+    {   // invariant divisor hm (>= 2): see div_by
+        int l = 0;
+        while ((int64_t(1) << l) < r.hm) ++l;
+        r.hm_mul = uint32_t((((uint64_t(1) << l) - uint64_t(r.hm)) << 32) / uint64_t(r.hm) + 1u);
+        r.hm_sh = l - 1;
+    }
     const int64_t ncell = int64_t(m) * m;
     r.nt = o.trials_per_cell > 0 ? o.trials_per_cell : int((N + ncell - 1) / ncell);
     r.W = int32_t(W);

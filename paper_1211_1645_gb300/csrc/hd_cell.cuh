@@ -188,7 +188,10 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
 // uniform in [-delta, delta]^2, rejected if it leaves the cell or comes
 // closer than 2 sigma to another occupant or to a disk of the eight
 // neighbouring cells (`neighbours_clear(np)`).  Updates P; returns accepts.
-template <bool FIX, int CAP, class NbrClear>
+// NT1: rep.nt is known to be 1 (one trial per occupied cell, the usual case
+// at liquid and solid densities), which lets the compiler keep every value's
+// live range to the single trial.
+template <bool FIX, int CAP, bool NT1 = false, class NbrClear>
 __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
                                              NbrClear&& neighbours_clear) {
     uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
@@ -228,7 +231,8 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
         }
     }
     uint32_t acc = 0;
-    for (int t = 0; t < rep.nt; ++t) {
+    const int nt = NT1 ? 1 : rep.nt;
+    for (int t = 0; t < nt; ++t) {
         const uint4 u = (FIX && t == 0) ? u0 : philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
         const int slot = int((order >> (4 * (n == 1 ? 0 : t % n))) & 0xFull);
         P2<FIX> me = P[0];
@@ -247,12 +251,14 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
             np.y = __dadd_rn(me.y, step_fp64(u.z, u.w, rep.delta));
             ok = np.x >= 0.0 && np.x < rep.w && np.y >= 0.0 && np.y < rep.w;
         }
-        if (ok) {
+        // The tests run whatever the boundary test said (a warp rarely skips
+        // them all), without branches: a slot that is not an occupant, or the
+        // moving disk itself, masks its own result.  A move outside the cell
+        // keeps every difference within int32 (|dx| < 3W).
 #pragma unroll
-            for (int q = 0; q < CAP; ++q)
-                if (q < n && q != slot) ok = ok && pair_clear<FIX>(P[q], 0, 0, np, rep);
-            ok = ok && neighbours_clear(np);
-        }
+        for (int q = 0; q < CAP; ++q)
+            ok &= pair_clear<FIX>(P[q], 0, 0, np, rep) | (q >= n) | (q == slot);
+        if (FIX || ok) ok &= neighbours_clear(np);  // the FP64 form loads neighbours lazily: skip when rejected
         if (ok) {
 #pragma unroll
             for (int q = 0; q < CAP; ++q)
@@ -266,23 +272,21 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
 // Sum two per-thread counters over the block and add them to counters[2r],
 // counters[2r + 1] with one atomic each.  Every thread of the block must call.
 __device__ __forceinline__ void block_count(uint32_t att, uint32_t acc, unsigned long long* counters, int r) {
-    __shared__ unsigned int s_att[32], s_acc[32];
+    __shared__ unsigned int s_cnt[2][32];
     att = __reduce_add_sync(0xffffffffu, att);
     acc = __reduce_add_sync(0xffffffffu, acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        s_att[warp] = att;
-        s_acc[warp] = acc;
+        s_cnt[0][warp] = att;
+        s_cnt[1][warp] = acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long ta = 0, tc = 0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
-            ta += s_att[w];
-            tc += s_acc[w];
-        }
-        if (ta) atomicAdd(&counters[2 * r], ta);
-        if (tc) atomicAdd(&counters[2 * r + 1], tc);
+    if (warp == 0) {
+        const bool live = lane < int(blockDim.x >> 5);
+        const unsigned int ta = __reduce_add_sync(0xffffffffu, live ? s_cnt[0][lane] : 0u);
+        const unsigned int tc = __reduce_add_sync(0xffffffffu, live ? s_cnt[1][lane] : 0u);
+        if (lane == 0 && ta) atomicAdd(&counters[2 * r], (unsigned long long)ta);
+        if (lane == 1 && tc) atomicAdd(&counters[2 * r + 1], (unsigned long long)tc);
     }
 }
 

@@ -31,9 +31,10 @@ struct Rep {
     int32_t blk_cell;   // first block of the replica in whole-cell grids
     int32_t blk_act;    // first block of the replica in active-cell grids
     int32_t blk_tile;   // first block of the replica in fused-sweep tile grids
-    int32_t pad_;
+    uint32_t hm_mul;    // hm_mul, hm_sh: divide by hm with div_by
     int32_t W, D;       // fixed point: cell side, maximum step (units 2^-24 sigma)
     int32_t hist_R;     // cell reach of the contact histogram
+    int32_t hm_sh;
     double w, w_below;  // FP64 cell side and the largest double below it
     double L, delta;    // FP64 box side and maximum step (sigma units)
     double Lm;          // realised box side (fixed form: m W 2^-24) for g(r) and eta
@@ -56,18 +57,16 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
                                         uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        if (round > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const uint32_t y0 = hi1 ^ c1 ^ k0;
-        const uint32_t y2 = hi0 ^ c3 ^ k1;
+        const uint32_t rk0 = k0 + uint32_t(round) * 0x9E3779B9u;
+        const uint32_t rk1 = k1 + uint32_t(round) * 0xBB67AE85u;
+        const uint64_t p0 = uint64_t(0xD2511F53u) * c0;  // one 32x32 -> 64 multiply per word
+        const uint64_t p1 = uint64_t(0xCD9E8D57u) * c2;
+        const uint32_t y0 = uint32_t(p1 >> 32) ^ c1 ^ rk0;
+        const uint32_t y2 = uint32_t(p0 >> 32) ^ c3 ^ rk1;
         c0 = y0;
-        c1 = lo1;
+        c1 = uint32_t(p1);
         c2 = y2;
-        c3 = lo0;
+        c3 = uint32_t(p0);
     }
     return make_uint4(c0, c1, c2, c3);
 }
@@ -84,6 +83,16 @@ __device__ __forceinline__ void pdl_begin() {
 // floor(word * n / 2^32): an integer in [0, n).
 __device__ __forceinline__ uint32_t bounded(uint32_t word, uint32_t n) { return __umulhi(word, n); }
 
+// n / d for a divisor d >= 2 fixed per replica, by one multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d),
+// mul = floor(2^32 (2^l - d) / d) + 1 and sh = l - 1, t = umulhi(mul, n)
+// and q = (t + ((n - t) >> 1)) >> sh, exact for every 32-bit n.
+__device__ __forceinline__ uint32_t div_by(uint32_t n, uint32_t mul, int sh) {
+    const uint32_t t = __umulhi(mul, n);
+    return (t + ((n - t) >> 1)) >> sh;
+}
+
 __device__ __forceinline__ int wrap_cell(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
 
 // Cells are stored in four colour planes (parities of cx and cy), each an
@@ -95,12 +104,13 @@ __host__ __device__ __forceinline__ int64_t cell_index(const Rep& r, int cx, int
     return r.cell_off + int64_t(((cy & 1) << 1) | (cx & 1)) * r.hm * r.hm + int64_t(cy >> 1) * r.hm + (cx >> 1);
 }
 
-// Inverse of cell_index for a replica-local planar position a in [0, m^2).
+// Inverse of cell_index for a replica-local planar position a in [0, m^2)
+// (the plane by three comparisons, the row by div_by).
 __device__ __forceinline__ void cell_coords(const Rep& r, int64_t a, int& cx, int& cy) {
     const uint32_t au = uint32_t(a), hh = uint32_t(r.hh), hm = uint32_t(r.hm);
-    const uint32_t plane = au / hh;
+    const uint32_t plane = uint32_t(au >= hh) + uint32_t(au >= 2u * hh) + uint32_t(au >= 3u * hh);
     const uint32_t rem = au - plane * hh;
-    const uint32_t row = rem / hm;
+    const uint32_t row = div_by(rem, r.hm_mul, r.hm_sh);
     cx = 2 * int(rem - row * hm) + int(plane & 1);
     cy = 2 * int(row) + int(plane >> 1);
 }

@@ -15,6 +15,8 @@
 // in the sweep's random order.  Cells of one colour are never neighbours, so
 // every thread of a pass owns its cell outright and only reads the
 // (unchanging) cells of the other colours.
+#include <mutex>
+
 #include "hd_cell.cuh"
 #include "hd_kernels.h"
 
@@ -120,17 +122,35 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
 
 // ---------------------------------------------------------------------------
 // One colour pass: every active cell shuffles its occupants and makes nt
-// serial trial moves (try_cell).  The cell and its eight neighbours are
-// loaded before the draws are made, so the generator's arithmetic overlaps the
-// load latency (the FP64 form, whose slots are twice as wide, loads one
-// neighbour at a time inside the test).
+// serial trial moves (try_cell).  The loads of the cell and its eight
+// neighbours are issued before the draws are made, so the generator's
+// arithmetic overlaps their latency.  In the fixed-point form the first two
+// slots of each neighbour are copied into the thread's own shared-memory
+// area with cp.async, which holds no register while the copy is in flight;
+// that halves the registers of the kernel and doubles the resident warps
+// that hide the latency.  (The FP64 form, whose slots are twice as wide,
+// loads one neighbour at a time inside the test.)
 // ---------------------------------------------------------------------------
-template <bool FIX, int CAP>
+// Per-thread shared area of the fixed form: 8 neighbours x kEagerSlots slots,
+// plus one pad entry so that a warp's 8-byte accesses take the minimum two
+// shared-memory wavefronts.
+constexpr int kNbrStride = 17;
+
+size_t pass_smem(bool fixed, int threads) {
+    return fixed ? size_t(threads) * kNbrStride * sizeof(int2) : 0;
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <bool FIX, int CAP, bool NT1>
 __global__ void __launch_bounds__(256)
 k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int j, int p,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
     pdl_begin();
-    constexpr bool kAllCells = FIX;
+    extern __shared__ int2 s_nbr[];
     const int r = find_rep<kGridAct>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
     const int m = rep.m, hm = rep.hm;
@@ -139,7 +159,7 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
     const int col = int(f.perm >> (2 * p)) & 3;
     uint32_t att = 0, acc = 0;
     if (a < uint32_t(rep.hh)) {
-        const uint32_t row = a / uint32_t(hm);
+        const uint32_t row = div_by(a, rep.hm_mul, rep.hm_sh);
         const int cx = 2 * int(a - row * uint32_t(hm)) + (col & 1);
         const int cy = 2 * int(row) + (col >> 1);
         const uint32_t cl = uint32_t(cy) * uint32_t(m) + uint32_t(cx);  // Philox counter: row-major cell
@@ -150,14 +170,24 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
             xp[o] = col_part(rep, wrap_cell(cx + o - 1, m));
             yp[o] = rep.coff + row_part(rep, wrap_cell(cy + o - 1, m));
         }
-        CellRegs<FIX, false> nb[kAllCells ? 9 : 1];
+        // Fixed form: neighbour i (0..8, centre skipped as nbr index q) has its
+        // occupancy in bits 4q..4q+3 of nocc and slots 0, 1 in mine[2q], mine[2q + 1].
+        int2* mine = s_nbr + threadIdx.x * kNbrStride;
+        uint32_t nocc = 0;
+        if constexpr (FIX) {
+            const uint32_t sm = static_cast<uint32_t>(__cvta_generic_to_shared(mine));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (i == 4) continue;
+                const int q = i < 4 ? i : i - 1;
+                const uint32_t ci = yp[i / 3] + xp[i % 3];
+                nocc |= uint32_t(occupancy<CAP>(cnt, ci)) << (4 * q);
+                cp_async8(sm + uint32_t(2 * q) * 8u, pos + ci);
+                cp_async8(sm + uint32_t(2 * q + 1) * 8u, pos + rep.stride32 + ci);
+            }
+        }
         CellRegs<FIX, true> own;
         load_cell<FIX, true, CAP>(cnt, pos, pid, rep.stride32, cell, own);
-        if constexpr (kAllCells) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                if (i != 4) load_cell<FIX, false, CAP>(cnt, pos, nullptr, rep.stride32, yp[i / 3] + xp[i % 3], nb[i]);
-        }
         const int n = own.n;
         if (n > 0) {
             // occupants in ascending id: the base order of the shuffle
@@ -172,20 +202,37 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
             if (n > 1) sort_by_id<FIX, CAP>(P, ids, n);
             auto neighbours_clear = [&](const P2<FIX>& np) {
                 bool ok = true;
-                if constexpr (kAllCells) {
+                if constexpr (FIX) {
+                    cp_async_wait_all();  // a no-op after the first trial
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         if (i == 4) continue;
+                        const int q = i < 4 ? i : i - 1;
                         const int ox = i % 3 - 1, oy = i / 3 - 1;
+                        const int ni = int(nocc >> (4 * q)) & 0xF;
+                        ok &= pair_clear<FIX>(mine[2 * q], ox, oy, np, rep) | (ni < 1);
+                        ok &= pair_clear<FIX>(mine[2 * q + 1], ox, oy, np, rep) | (ni < 2);
+                    }
+                    // Neighbours holding more than kEagerSlots disks (rare): a
+                    // nibble n >= 3 is the one whose n + 5 sets its bit 3.
+                    if ((nocc + 0x55555555u) & 0x88888888u) {
 #pragma unroll
-                        for (int k = 0; k < kEagerSlots; ++k)
-                            if (k < nb[i].n) ok = ok && pair_clear<FIX>(nb[i].s[k], ox, oy, np, rep);
-                        for (int k = kEagerSlots; k < nb[i].n; ++k)
-                            ok = ok && pair_clear<FIX>(nb[i].slot(k, pos, rep.stride32), ox, oy, np, rep);
+                        for (int i = 0; i < 9; ++i) {
+                            if (i == 4) continue;
+                            const int q = i < 4 ? i : i - 1;
+                            const int ni = int(nocc >> (4 * q)) & 0xF;
+                            // the cell index is recomputed here, so that no register keeps it
+                            const uint32_t ci = rep.coff + row_part(rep, wrap_cell(cy + i / 3 - 1, m)) +
+                                                col_part(rep, wrap_cell(cx + i % 3 - 1, m));
+                            for (int k = kEagerSlots; k < ni; ++k)
+                                ok &= pair_clear<FIX>(__ldg(pos + size_t(k) * rep.stride32 + ci), i % 3 - 1, i / 3 - 1,
+                                                      np, rep);
+                        }
                     }
                 } else {
-                    for (int i = 0; i < 9 && ok; ++i) {
-                        if (i == 4) continue;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        if (i == 4 || !ok) continue;
                         const int ox = i % 3 - 1, oy = i / 3 - 1;
                         CellRegs<FIX, false> c;
                         load_cell<FIX, false, CAP>(cnt, pos, nullptr, rep.stride32, yp[i / 3] + xp[i % 3], c);
@@ -194,7 +241,7 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                 }
                 return ok;
             };
-            acc = try_cell<FIX, CAP>(rep, f.sweep, cl, P, n, neighbours_clear);
+            acc = try_cell<FIX, CAP, NT1>(rep, f.sweep, cl, P, n, neighbours_clear);
             att = uint32_t(rep.nt);
             // written back in id order (the ids too, since the sort may have permuted them)
             if (acc > 0 || n > 1) {
@@ -208,6 +255,8 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                     if (q < n) pid[size_t(q) * rep.stride32 + cell] = ids[q];
             }
         }
+        // no copy may still be landing in shared memory when the thread exits
+        if constexpr (FIX) cp_async_wait_all();
     }
     block_count(att, acc, counters, r);
 }
@@ -270,17 +319,30 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
     return c.cap == 4 ? rebuild_t<false, 4>(c, table, j, from, to, err) : rebuild_t<false, 9>(c, table, j, from, to, err);
 }
 
-template <bool FIX, int CAP>
+template <bool FIX, int CAP, bool NT1>
 static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                           unsigned long long* counters) {
-    return launch_k(k_pass<FIX, CAP>, dim3(c.blocks_act), dim3(c.threads), 0, c.stream, c.reps, c.R, table, j, p,
-                    (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
+    const size_t smem = pass_smem(FIX, c.threads);
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [&] {
+        cudaFuncSetAttribute(k_pass<FIX, CAP, NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(pass_smem(FIX, 256)));
+    });
+    return launch_k(k_pass<FIX, CAP, NT1>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R, table,
+                    j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
+}
+
+template <bool FIX, int CAP>
+static cudaError_t pass_nt(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
+                           unsigned long long* counters) {
+    return c.nt1 ? pass_t<FIX, CAP, true>(c, table, j, p, cells, counters)
+                 : pass_t<FIX, CAP, false>(c, table, j, p, cells, counters);
 }
 
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters) {
-    if (c.fixed) return c.cap == 4 ? pass_t<true, 4>(c, table, j, p, cells, counters) : pass_t<true, 9>(c, table, j, p, cells, counters);
-    return c.cap == 4 ? pass_t<false, 4>(c, table, j, p, cells, counters) : pass_t<false, 9>(c, table, j, p, cells, counters);
+    if (c.fixed) return c.cap == 4 ? pass_nt<true, 4>(c, table, j, p, cells, counters) : pass_nt<true, 9>(c, table, j, p, cells, counters);
+    return c.cap == 4 ? pass_nt<false, 4>(c, table, j, p, cells, counters) : pass_nt<false, 9>(c, table, j, p, cells, counters);
 }
 
 template <bool FIX, int CAP>
