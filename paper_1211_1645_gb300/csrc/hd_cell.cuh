@@ -172,7 +172,11 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
     if constexpr (FIX) {
         const int32_t rx = (q.x + ox * rep.W) - np.x;
         const int32_t ry = (q.y + oy * rep.W) - np.y;
-        return (int64_t(rx) * rx + int64_t(ry) * ry) >= kFxDiam2;
+        // d^2 >= 2^50 exactly when the high word of the (non-negative, < 2^63)
+        // 64-bit square sum is >= 2^18: one 32-bit compare
+        const uint64_t d2 = uint64_t(int64_t(rx) * rx) + uint64_t(int64_t(ry) * ry);
+        static_assert(kFxDiam2 == (int64_t(1) << 50), "the high-word test assumes (2 sigma)^2 = 2^50");
+        return uint32_t(d2 >> 32) >= (1u << 18);
     } else {
         const double offx = ox < 0 ? -rep.w : (ox > 0 ? rep.w : 0.0);
         const double offy = oy < 0 ? -rep.w : (oy > 0 ? rep.w : 0.0);
