@@ -43,7 +43,7 @@ struct hd_ctx {
     std::vector<Rep> reps;
     std::vector<int64_t> nlat;
     int64_t Ntot = 0, Ctot = 0;
-    int blocks_cell = 0, blocks_act = 0, blocks_tile = 0;
+    int blocks_cell = 0, blocks_act = 0, blocks_tile = 0, blocks_t32 = 0;
     Rep* reps_d = nullptr;
     CellBufs buf[2] = {};
     int cur = 0;
@@ -103,6 +103,7 @@ struct hd_ctx {
         c.blocks_cell = blocks_cell;
         c.blocks_act = blocks_act;
         c.blocks_tile = blocks_tile;
+        c.blocks_t32 = blocks_t32;
         c.stream = stream;
         return c;
     }
@@ -484,7 +485,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         return HD_ERR_ARG;
     }
     int64_t cell_off = 0, id_off = 0;
-    int blk_cell = 0, blk_act = 0, blk_tile = 0;
+    int blk_cell = 0, blk_act = 0, blk_tile = 0, blk_t32 = 0;
     for (int r = 0; r < R; ++r) {
         Rep rep = plans[size_t(r)].rep;
         rep.cell_off = cell_off;
@@ -492,6 +493,17 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         rep.blk_cell = blk_cell;
         rep.blk_act = blk_act;
         rep.blk_tile = blk_tile;
+        rep.blk_t32 = blk_t32;
+        rep.tiles_x = (rep.m + 31) / 32;
+        rep.tx_mul = 0;
+        rep.tx_sh = 0;
+        if (rep.tiles_x > 1) {  // invariant divisor tiles_x >= 2: see div_by (tiles_x = 1 needs no division)
+            int l = 0;
+            while ((int64_t(1) << l) < rep.tiles_x) ++l;
+            rep.tx_mul = uint32_t((((uint64_t(1) << l) - uint64_t(rep.tiles_x)) << 32) / uint64_t(rep.tiles_x) + 1u);
+            rep.tx_sh = l - 1;
+        }
+        blk_t32 += int(int64_t(rep.tiles_x) * ((rep.m + ctx->threads / 32 - 1) / (ctx->threads / 32)));
         const int64_t tx = (rep.m + ctx->tile - 1) / ctx->tile;
         blk_tile += int(tx * tx);
         const int64_t ncell = int64_t(rep.m) * rep.m;
@@ -525,6 +537,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->blocks_cell = blk_cell;
     ctx->blocks_act = blk_act;
     ctx->blocks_tile = blk_tile;
+    ctx->blocks_t32 = blk_t32;
 
     const size_t slots = size_t(ctx->Ctot) * cap;
     bool ok = dev_alloc(ctx, &ctx->reps_d, size_t(R));
@@ -552,7 +565,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ok = ok && dev_alloc(ctx, &ctx->edgesF, size_t(ctx->K + 1));
     ok = ok && dev_alloc(ctx, &ctx->fit, size_t(4 * R));
     ok = ok && dev_alloc(ctx, &ctx->psi_local, size_t(ctx->Ntot));
-    ok = ok && dev_alloc(ctx, &ctx->psi_part, size_t(ctx->blocks_cell));
+    ok = ok && dev_alloc(ctx, &ctx->psi_part, size_t(ctx->blocks_t32));
     ok = ok && dev_alloc(ctx, &ctx->psi_res, size_t(2 * R));
     ok = ok && dev_alloc(ctx, &ctx->xy, size_t(2 * ctx->Ntot));
     if (!ok) {

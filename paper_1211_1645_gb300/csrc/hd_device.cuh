@@ -35,6 +35,10 @@ struct Rep {
     int32_t W, D;       // fixed point: cell side, maximum step (units 2^-24 sigma)
     int32_t hist_R;     // cell reach of the contact histogram
     int32_t hm_sh;
+    int32_t blk_t32;    // first block of the replica in 32-column tile grids (32 x threads/32 cells)
+    int32_t tiles_x;    // such tiles per row of cells, ceil(m / 32)
+    uint32_t tx_mul;    // tx_mul, tx_sh: divide by tiles_x >= 2 with div_by
+    int32_t tx_sh;
     double w, w_below;  // FP64 cell side and the largest double below it
     double L, delta;    // FP64 box side and maximum step (sigma units)
     double Lm;          // realised box side (fixed form: m W 2^-24) for g(r) and eta
@@ -93,6 +97,14 @@ __device__ __forceinline__ uint32_t div_by(uint32_t n, uint32_t mul, int sh) {
     return (t + ((n - t) >> 1)) >> sh;
 }
 
+// Origin (X0, Y0) of block b (replica-local) of a 32-column tile grid whose
+// tiles are 32 x rows cells, row-major over tiles.
+__device__ __forceinline__ void tile32_origin(const Rep& r, uint32_t b, int rows, int& X0, int& Y0) {
+    const uint32_t ty = r.tiles_x > 1 ? div_by(b, r.tx_mul, r.tx_sh) : b;
+    X0 = int(b - ty * uint32_t(r.tiles_x)) * 32;
+    Y0 = int(ty) * rows;
+}
+
 __device__ __forceinline__ int wrap_cell(int c, int m) { return c < 0 ? c + m : (c >= m ? c - m : c); }
 
 // Cells are stored in four colour planes (parities of cx and cy), each an
@@ -125,7 +137,7 @@ __device__ __forceinline__ uint32_t row_part(const Rep& r, int cy) {
 }
 
 // Grids over all replicas: whole cells, active cells of one colour, tiles.
-enum GridKind { kGridCell = 0, kGridAct = 1, kGridTile = 2 };
+enum GridKind { kGridCell = 0, kGridAct = 1, kGridTile = 2, kGridT32 = 3 };
 
 // Replica owning block `blk`, given per-replica first blocks (ascending).
 template <int KIND>
@@ -133,7 +145,10 @@ __device__ __forceinline__ int find_rep(const Rep* __restrict__ reps, int R, int
     int lo = 0, hi = R - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int start = KIND == kGridAct ? reps[mid].blk_act : (KIND == kGridTile ? reps[mid].blk_tile : reps[mid].blk_cell);
+        const int start = KIND == kGridAct    ? reps[mid].blk_act
+                          : KIND == kGridTile ? reps[mid].blk_tile
+                          : KIND == kGridT32  ? reps[mid].blk_t32
+                                              : reps[mid].blk_cell;
         if (start <= blk) lo = mid; else hi = mid - 1;
     }
     return lo;

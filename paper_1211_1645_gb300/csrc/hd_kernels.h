@@ -28,6 +28,7 @@ struct LaunchCfg {
     int blocks_cell;   // whole-cell grid size (all replicas)
     int blocks_act;    // active-cell grid size (all replicas)
     int blocks_tile;   // fused-sweep tile grid size (all replicas)
+    int blocks_t32;    // 32 x (threads / 32) cell-tile grid size (all replicas)
     cudaStream_t stream;
 };
 

@@ -6,6 +6,7 @@
 // Pair vectors are formed in the cell frame: for disks i and j whose cells
 // differ by (dcx, dcy), r = (u_j + dcx * w) - u_i, which is exact in the
 // fixed-point form and has one fixed rounding order in FP64.
+#include <mutex>
 #include <type_traits>
 
 #include "hd_kernels.h"
@@ -232,69 +233,133 @@ __device__ __forceinline__ void scan_cell(const Rep& rep, const uint8_t* __restr
     }
 }
 
+// Cover test of the ring search: the sixth neighbour is strictly closer than
+// any point outside the (2 RR + 1)^2 cells around the disk's cell.
+template <bool FIX>
+__device__ __forceinline__ bool ring_covers(const Rep& rep, const Nbr<FIX>& nb, const P2<FIX>& me, int RR) {
+    if (nb.n < 6) return false;
+    if constexpr (FIX) {
+        long long cv = static_cast<long long>(me.x) + static_cast<long long>(RR) * rep.W;
+        const long long c2 = static_cast<long long>(RR + 1) * rep.W - me.x;
+        const long long c3 = static_cast<long long>(me.y) + static_cast<long long>(RR) * rep.W;
+        const long long c4 = static_cast<long long>(RR + 1) * rep.W - me.y;
+        cv = c2 < cv ? c2 : cv;
+        cv = c3 < cv ? c3 : cv;
+        cv = c4 < cv ? c4 : cv;
+        return nb.key[5] < cv * cv;
+    } else {
+        double cv = __dadd_rn(me.x, __dmul_rn(double(RR), rep.w));
+        const double c2 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.x);
+        const double c3 = __dadd_rn(me.y, __dmul_rn(double(RR), rep.w));
+        const double c4 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.y);
+        cv = c2 < cv ? c2 : cv;
+        cv = c3 < cv ? c3 : cv;
+        cv = c4 < cv ? c4 : cv;
+        return nb.key[5] < __dmul_rn(cv, cv);
+    }
+}
+
+// Shared-memory copy of the cells a psi_6 block reads: its 32 x rows tile of
+// cells plus a halo of two cells (the 5 x 5 stencil of every tile cell).
+constexpr int kPsiHalo = 2;
+constexpr int kPsiSX = 32 + 2 * kPsiHalo;
+
+template <bool FIX, int CAP>
+__host__ __device__ constexpr size_t psi6_stage_bytes(int rows) {
+    return size_t(kPsiSX) * size_t(rows + 2 * kPsiHalo) * (CAP * (sizeof(P2<FIX>) + sizeof(int32_t)) + 1);
+}
+
+// psi_6 of every disk.  A block stages its tile and halo in shared memory in
+// one cooperative round of loads; each disk then scans its 5 x 5 stencil
+// there, nearest cells first (so the six-neighbour list fills early and most
+// later candidates are rejected by one comparison).  The rare disk whose six
+// neighbours are not certified by the 5 x 5 stencil (low density) continues
+// the ring search in global memory.
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
        const int32_t* __restrict__ pid, double2* __restrict__ local, double2* __restrict__ partial,
        int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
     pdl_begin();
-    const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
+    const int r = find_rep<kGridT32>(reps, R, blockIdx.x);
     const Rep& rep = reps[r];
     const int m = rep.m;
-    const int64_t a = int64_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
+    const int rows = int(blockDim.x >> 5);
+    int X0, Y0;
+    tile32_origin(rep, uint32_t(blockIdx.x - rep.blk_t32), rows, X0, Y0);
+    const int nS = kPsiSX * (rows + 2 * kPsiHalo);
+    P2<FIX>* s_pos = reinterpret_cast<P2<FIX>*>(s_raw);                  // [CAP][nS]
+    int32_t* s_id = reinterpret_cast<int32_t*>(s_pos + size_t(CAP) * nS);  // [CAP][nS]
+    uint8_t* s_n = reinterpret_cast<uint8_t*>(s_id + size_t(CAP) * nS);    // [nS]
+    for (int t = threadIdx.x; t < nS; t += blockDim.x) {
+        const int sy = t / kPsiSX, sx = t - sy * kPsiSX;
+        const uint32_t c = uint32_t(rep.coff) + row_part(rep, wrap_cell(Y0 - kPsiHalo + sy, m)) +
+                           col_part(rep, wrap_cell(X0 - kPsiHalo + sx, m));
+        const int n = min(int(cnt[c]), CAP);
+        s_n[t] = uint8_t(n);
+        for (int q = 0; q < n; ++q) {
+            s_pos[q * nS + t] = pos[size_t(q) * rep.stride32 + c];
+            s_id[q * nS + t] = pid[size_t(q) * rep.stride32 + c];
+        }
+    }
+    __syncthreads();
+
     double sr = 0.0, si = 0.0;
-    if (a < int64_t(m) * m) {
-        int cx, cy;
-        cell_coords(rep, a, cx, cy);
-        const int64_t cell = rep.cell_off + a;
-        const int n = min(int(cnt[cell]), CAP);
+    const int lx = int(threadIdx.x & 31u), ly = int(threadIdx.x >> 5);
+    const int cx = X0 + lx, cy = Y0 + ly;
+    if (cx < m && cy < m) {
+        const int own = (ly + kPsiHalo) * kPsiSX + lx + kPsiHalo;
+        const int n = s_n[own];
         int rmax = (m - 1) / 2;
         if constexpr (FIX) {
             const int lim = int((int64_t(1) << 31) / rep.W) - 1;
             if (lim < rmax) rmax = lim;
         }
         for (int k = 0; k < n; ++k) {
-            const P2<FIX> me = pos[k * rep.stride + cell];
-            const int32_t idme = pid[k * rep.stride + cell];
+            const P2<FIX> me = s_pos[k * nS + own];
+            const int32_t idme = s_id[k * nS + own];
             Nbr<FIX> nb;
             nb.n = 0;
             bool ok = false;
-            for (int RR = 2; RR <= rmax && !ok; ++RR) {
-                if (RR == 2) {
-                    for (int dcy = -2; dcy <= 2; ++dcy)
-                        for (int dcx = -2; dcx <= 2; ++dcx)
-                            scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, dcx, dcy, me, idme, nb);
-                } else {
-                    for (int e = -RR; e <= RR; ++e) {
-                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, -RR, me, idme, nb);
-                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, RR, me, idme, nb);
-                    }
-                    for (int e = -RR + 1; e <= RR - 1; ++e) {
-                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, -RR, e, me, idme, nb);
-                        scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, RR, e, me, idme, nb);
-                    }
-                }
-                if (nb.n == 6) {
-                    if constexpr (FIX) {
-                        long long cv = static_cast<long long>(me.x) + static_cast<long long>(RR) * rep.W;
-                        const long long c2 = static_cast<long long>(RR + 1) * rep.W - me.x;
-                        const long long c3 = static_cast<long long>(me.y) + static_cast<long long>(RR) * rep.W;
-                        const long long c4 = static_cast<long long>(RR + 1) * rep.W - me.y;
-                        cv = c2 < cv ? c2 : cv;
-                        cv = c3 < cv ? c3 : cv;
-                        cv = c4 < cv ? c4 : cv;
-                        ok = nb.key[5] < cv * cv;
-                    } else {
-                        double cv = __dadd_rn(me.x, __dmul_rn(double(RR), rep.w));
-                        const double c2 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.x);
-                        const double c3 = __dadd_rn(me.y, __dmul_rn(double(RR), rep.w));
-                        const double c4 = __dsub_rn(__dmul_rn(double(RR + 1), rep.w), me.y);
-                        cv = c2 < cv ? c2 : cv;
-                        cv = c3 < cv ? c3 : cv;
-                        cv = c4 < cv ? c4 : cv;
-                        ok = nb.key[5] < __dmul_rn(cv, cv);
+            if (rmax >= 2) {
+                // rings 0, 1, 2 of the staged stencil, nearest first
+#pragma unroll 1
+                for (int ring = 0; ring <= 2; ++ring) {
+                    for (int dcy = -ring; dcy <= ring; ++dcy) {
+                        for (int dcx = -ring; dcx <= ring; ++dcx) {
+                            if (max(abs(dcx), abs(dcy)) != ring) continue;
+                            const int sc = own + dcy * kPsiSX + dcx;
+                            const int nn = s_n[sc];
+                            for (int q = 0; q < nn; ++q) {
+                                const int32_t idq = s_id[q * nS + sc];
+                                if (idq == idme) continue;
+                                const P2<FIX> o = s_pos[q * nS + sc];
+                                if constexpr (FIX) {
+                                    const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
+                                    const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
+                                    nb.insert(rx * rx + ry * ry, idq, rx, ry);
+                                } else {
+                                    const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
+                                    const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
+                                    nb.insert(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), idq, rx, ry);
+                                }
+                            }
+                        }
                     }
                 }
+                ok = ring_covers<FIX>(rep, nb, me, 2);
+            }
+            for (int RR = 3; RR <= rmax && !ok; ++RR) {
+                for (int e = -RR; e <= RR; ++e) {
+                    scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, -RR, me, idme, nb);
+                    scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, e, RR, me, idme, nb);
+                }
+                for (int e = -RR + 1; e <= RR - 1; ++e) {
+                    scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, -RR, e, me, idme, nb);
+                    scan_cell<FIX, CAP>(rep, cnt, pos, pid, cx, cy, RR, e, me, idme, nb);
+                }
+                ok = ring_covers<FIX>(rep, nb, me, RR);
             }
             double pre, pim;
             if (!ok) {
@@ -372,8 +437,8 @@ __global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_to
     pdl_begin();
     const int r = blockIdx.x;
     const Rep& rep = reps[r];
-    const int b0 = rep.blk_cell;
-    const int b1 = (r + 1 < R) ? reps[r + 1].blk_cell : blocks_total;
+    const int b0 = rep.blk_t32;
+    const int b1 = (r + 1 < R) ? reps[r + 1].blk_t32 : blocks_total;
     double sr = 0.0, si = 0.0;
     for (int b = b0 + int(threadIdx.x); b < b1; b += blockDim.x) {
         sr += partial[b].x;
@@ -418,7 +483,13 @@ cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist
 
 template <bool FIX, int CAP>
 static cudaError_t psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
-    return launch_k(k_psi6<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), 0, c.stream, c.reps, c.R,
+    const size_t smem = psi6_stage_bytes<FIX, CAP>(c.threads / 32);
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        cudaFuncSetAttribute(k_psi6<FIX, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(psi6_stage_bytes<FIX, CAP>(8)));
+    });
+    return launch_k(k_psi6<FIX, CAP>, dim3(c.blocks_t32), dim3(c.threads), smem, c.stream, c.reps, c.R,
                     (const uint8_t*)cells.cnt, (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid, local, partial,
                     err);
 }
@@ -453,7 +524,7 @@ cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* p
 }
 
 cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res) {
-    return launch_k(k_psi6_reduce, dim3(c.R), dim3(256), 0, c.stream, c.reps, c.R, c.blocks_cell, partial, res);
+    return launch_k(k_psi6_reduce, dim3(c.R), dim3(256), 0, c.stream, c.reps, c.R, c.blocks_t32, partial, res);
 }
 
 }  // namespace hd
