@@ -11,6 +11,12 @@ Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the library's stream; L2 is flushed (a 256 MB write) before every timed
 step, outside the events.  Under torchrun each rank runs its own replica
 (seed + rank, weak scaling) and rank 0 reports the max time over ranks.
+Each step is one graph launch of the library (hd_run).
+
+Secondary keys of the same line (same step and timing): `fp64` (the plain
+FP64 chain), `replicas4` (four replicas of the headline system in one
+context), `scan31` (the 31-replica equation-of-state scan) and `autotuned`
+(the headline system at the cell side and block size the autotuner picks).
 
 --impl reference times the CPU oracle (one core) on a bounded sample of the
 same workload instead.
@@ -49,9 +55,10 @@ def parse_args(argv=None):
     p.add_argument("--cell-min", type=float, default=2.0, help="minimum cell side in sigma (>= 2)")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--form", choices=["fixed", "fp64"], default="fixed")
-    p.add_argument("--sweep-kernel", choices=["split", "fused"], default="split")
+    p.add_argument("--sweep-kernel", choices=["split", "tma", "fused"], default="split")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the replica, scan and autotuned lines")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU oracle sample budget")
     return p.parse_args(argv)
@@ -149,16 +156,30 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def time_form(args, form, rank, world, steps, warmup, sampler=None):
-    """Device-resident timing of `steps` steps of one form; returns a dict."""
+def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
+              block_threads=128, sweep_kernel=None):
+    """Device-resident timing of `steps` steps of one form; returns a dict.
+    N and eta may be per-replica lists (one batched context); attempts are
+    summed over replicas."""
+    import numpy as np
     import torch
 
     import paper_1211_1645_gb300 as hd
 
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
-    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form,
-                        sweep_kernel=args.sweep_kernel, cell_min=args.cell_min)
+    N = args.N if N is None else N
+    eta = args.eta if eta is None else eta
+    if np.ndim(N) == 0:
+        sysg = hd.HardDisks(N, eta, args.delta, args.seed + rank, precision=form,
+                            sweep_kernel=sweep_kernel or args.sweep_kernel,
+                            cell_min=cell_min or args.cell_min, block_threads=block_threads)
+    else:
+        R = len(N)
+        seeds = [args.seed + rank * R + r for r in range(R)]
+        sysg = hd.HardDisks(list(N), list(eta), [args.delta] * R, seeds, precision=form,
+                            sweep_kernel=sweep_kernel or args.sweep_kernel,
+                            cell_min=cell_min or args.cell_min, block_threads=block_threads)
     sysg.set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     S = args.sweeps_per_step
@@ -172,7 +193,7 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    att0 = int(sysg.stats()[0][0])
+    att0 = int(sysg.stats()[0].sum())
     l0 = sysg.kernel_times()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier(world)
@@ -189,8 +210,8 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     barrier(world)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     att1, acc1 = sysg.stats()
-    attempts = int(att1[0]) - att0
-    acceptance = float(acc1[0]) / float(att1[0]) if int(att1[0]) else None
+    attempts = int(att1.sum()) - att0
+    acceptance = float(acc1.sum()) / float(att1.sum()) if int(att1.sum()) else None
     l1 = sysg.kernel_times()
     launches = sum(l1[k][1] - l0[k][1] for k in l1)
 
@@ -207,6 +228,46 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None):
     return {"ms": ms, "attempts": attempts, "launches": launches, "clocks": clocks, "kernel_times": kt,
             "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None,
             "acceptance": acceptance}
+
+
+# The equation-of-state scan: replica r has N = SCAN_N[r mod 5], eta = 0.700 + 0.001 r.
+SCAN_N = [128 ** 2, 192 ** 2, 256 ** 2, 384 ** 2, 512 ** 2]
+
+
+def time_extras(args, rank, world, dev):
+    """Secondary lines, same step definition and timing as the headline:
+    four replicas of the headline system in one context, the 31-replica
+    equation-of-state scan, and the headline system at the cell side, sweep
+    kernel and block size the autotuner picks (sweeps only, then re-timed
+    with measurement and L2 flush)."""
+    from paper_1211_1645_gb300.tune import autotune
+    out = {}
+    steps, warm = max(1, args.steps // 2), 2
+    r4 = time_form(args, args.form, rank, world, steps, warm, N=[args.N] * 4, eta=[args.eta] * 4)
+    t, a = reduce_max_sum(world, r4["ms"], float(r4["attempts"]), dev)
+    out["replicas4"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
+                        "config": f"4 replicas x N={args.N}, eta={args.eta}, one context"}
+    R = 31
+    Ns = [SCAN_N[r % 5] for r in range(R)]
+    etas = [0.700 + 0.001 * r for r in range(R)]
+    rs = time_form(args, args.form, rank, world, steps, warm, N=Ns, eta=etas)
+    t, a = reduce_max_sum(world, rs["ms"], float(rs["attempts"]), dev)
+    out["scan31"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
+                     "config": f"31 replicas, N = {{128^2 .. 512^2}} round-robin ({sum(Ns)} disks), "
+                               "eta = 0.700 + 0.001 r, one context"}
+    best, table = autotune(args.N, args.eta, args.delta, args.seed + rank, precision=args.form,
+                           cell_mins=(2.0, 2.2, 2.4), kernels=("split",), block_threads=(128, 256),
+                           sweeps=args.sweeps_per_step, steps=2)
+    if best:
+        rt = time_form(args, args.form, rank, world, steps, warm, cell_min=best["cell_min"],
+                       block_threads=best["block_threads"], sweep_kernel=best["sweep_kernel"])
+        t, a = reduce_max_sum(world, rt["ms"], float(rt["attempts"]), dev)
+        out["autotuned"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
+                            "choice": {k: best[k] for k in ("cell_min", "sweep_kernel", "block_threads",
+                                                            "cells_per_side", "trials_per_cell")},
+                            "candidates": [{k: c[k] for k in ("cell_min", "block_threads", "trial_moves_per_s")}
+                                           for c in table]}
+    return out
 
 
 def time_e2e(args, form, rank, steps):
@@ -327,6 +388,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2))
+    extras = None if args.no_extras else time_extras(args, rank, world, dev)
     if rank != 0:
         return
     kt = main["kernel_times"]
@@ -368,6 +430,8 @@ def run_ours(args):
         "fp64": fp64,
         "e2e": e2e,
     }
+    if extras:
+        line.update(extras)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(args, args.form, args.cpu_seconds)
     print(json.dumps(line), flush=True)

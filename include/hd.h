@@ -64,12 +64,17 @@ typedef struct hd_opts {
     double cell_min;         /* minimum cell side in sigma, >= 2 [2]; Sec. II.B     */
     int32_t block_threads;   /* threads per block of the split sweep kernels [128]  */
     int32_t sweep_kernel;    /* HD_SWEEP_SPLIT: a rebuild launch and four colour-pass
-                                launches per sweep [default]; HD_SWEEP_FUSED: one
+                                launches per sweep, each pass thread copying its
+                                neighbours with cp.async [default]; HD_SWEEP_TMA:
+                                the same launches, each pass block staging its
+                                neighbourhood (six row segments of the colour
+                                planes) with bulk copies (TMA); HD_SWEEP_FUSED: one
                                 launch per sweep, tiles staged in shared memory.
-                                Both give bit-identical chains.                     */
+                                All give bit-identical chains.  A bulk-copy pass
+                                that cannot stage its segments sets HD_ERR_TIMEOUT. */
 } hd_opts;
 
-enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1 };
+enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1, HD_SWEEP_TMA = 2 };
 
 /* Geometry of one replica as realised by the library. */
 typedef struct hd_geometry {

@@ -20,6 +20,7 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kFx = 16777216.0;  // 2^24 fixed-point units per sigma
 constexpr int kMaxBins = 512;
+constexpr size_t kCellPad = 64;  // elements of padding after every per-generation cell array
 
 struct Plan {
     Rep rep;
@@ -38,12 +39,13 @@ struct hd_ctx {
     int lattice = 0;
     int threads = 128;
     bool fused = false;
+    bool pass_tma = false;  // colour pass with bulk-copy (TMA) staging
     int tile = 48;
     double sigma = 1.0;
     std::vector<Rep> reps;
     std::vector<int64_t> nlat;
     int64_t Ntot = 0, Ctot = 0;
-    int blocks_cell = 0, blocks_act = 0, blocks_tile = 0, blocks_t32 = 0;
+    int blocks_cell = 0, blocks_act = 0, blocks_tile = 0, blocks_t32 = 0, blocks_seg = 0;
     Rep* reps_d = nullptr;
     CellBufs buf[2] = {};
     int cur = 0;
@@ -104,6 +106,7 @@ struct hd_ctx {
         c.blocks_act = blocks_act;
         c.blocks_tile = blocks_tile;
         c.blocks_t32 = blocks_t32;
+        c.blocks_seg = blocks_seg;
         c.stream = stream;
         return c;
     }
@@ -282,6 +285,10 @@ hd_status check_flags(hd_ctx* ctx) {
         ctx->sticky = HD_ERR_OVERFLOW;
         return HD_ERR_OVERFLOW;
     }
+    if (flag & 8) {  // a staging copy of the bulk-copy pass was refused or did not complete in time
+        ctx->sticky = HD_ERR_TIMEOUT;
+        return HD_ERR_TIMEOUT;
+    }
     if (flag & 2) {
         HD_CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
         HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -361,7 +368,9 @@ cudaError_t enqueue_sweeps(hd_ctx* ctx, cudaStream_t s, int64_t n, bool capturin
                 ctx->cur ^= 1;
                 for (int p = 0; p < 4 && e == cudaSuccess; ++p)
                     e = launch(ctx, HD_K_PASS, [&] {
-                        return hd::launch_pass(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters);
+                        return ctx->pass_tma
+                                   ? hd::launch_pass_tma(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters, ctx->err)
+                                   : hd::launch_pass(c, ctx->table, j, p, ctx->buf[ctx->cur], ctx->counters);
                     }, capturing);
             }
         }
@@ -456,7 +465,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
     if (!(o.cell_min >= 2.0) || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
     if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
-    if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT) return HD_ERR_ARG;
+    if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT && o.sweep_kernel != HD_SWEEP_TMA)
+        return HD_ERR_ARG;
 
     std::vector<Plan> plans(static_cast<size_t>(R));
     int cap = 4;
@@ -476,6 +486,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->lattice = o.lattice;
     ctx->threads = o.block_threads;
     ctx->fused = o.sweep_kernel == HD_SWEEP_FUSED;
+    ctx->pass_tma = o.sweep_kernel == HD_SWEEP_TMA;
     ctx->tile = hd::fused_tile(ctx->fixed, cap);
     ctx->sigma = sigma;
     ctx->sweeps.assign(size_t(R), 0);
@@ -485,7 +496,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         return HD_ERR_ARG;
     }
     int64_t cell_off = 0, id_off = 0;
-    int blk_cell = 0, blk_act = 0, blk_tile = 0, blk_t32 = 0;
+    int blk_cell = 0, blk_act = 0, blk_tile = 0, blk_t32 = 0, blk_seg = 0;
     for (int r = 0; r < R; ++r) {
         Rep rep = plans[size_t(r)].rep;
         rep.cell_off = cell_off;
@@ -504,6 +515,19 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
             rep.tx_sh = l - 1;
         }
         blk_t32 += int(int64_t(rep.tiles_x) * ((rep.m + ctx->threads / 32 - 1) / (ctx->threads / 32)));
+        rep.blk_seg = blk_seg;
+        rep.nseg = (rep.hm + ctx->threads - 1) / ctx->threads;
+        rep.segw = (rep.hm + rep.nseg - 1) / rep.nseg;
+        rep.seg_mul = 0;
+        rep.seg_sh = 0;
+        rep.pad_seg = 0;
+        if (rep.nseg > 1) {  // invariant divisor nseg >= 2: see div_by
+            int l = 0;
+            while ((int64_t(1) << l) < rep.nseg) ++l;
+            rep.seg_mul = uint32_t((((uint64_t(1) << l) - uint64_t(rep.nseg)) << 32) / uint64_t(rep.nseg) + 1u);
+            rep.seg_sh = l - 1;
+        }
+        blk_seg += rep.hm * rep.nseg;
         const int64_t tx = (rep.m + ctx->tile - 1) / ctx->tile;
         blk_tile += int(tx * tx);
         const int64_t ncell = int64_t(rep.m) * rep.m;
@@ -522,7 +546,9 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         ctx->reps.push_back(rep);
         ctx->nlat.push_back(plans[size_t(r)].nlat);
     }
-    ctx->Ctot = cell_off;
+    // cell arrays are padded to a multiple of 16 cells, so that every slot
+    // plane starts on a 16-byte boundary (bulk copies need one)
+    ctx->Ctot = (cell_off + 15) & ~int64_t(15);
     ctx->Ntot = id_off;
     if (ctx->Ctot * int64_t(cap) >= (int64_t(1) << 31)) {
         delete ctx;
@@ -538,20 +564,23 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->blocks_act = blk_act;
     ctx->blocks_tile = blk_tile;
     ctx->blocks_t32 = blk_t32;
+    ctx->blocks_seg = blk_seg;
 
     const size_t slots = size_t(ctx->Ctot) * cap;
     bool ok = dev_alloc(ctx, &ctx->reps_d, size_t(R));
     for (int b = 0; b < 2 && ok; ++b) {
         // occupancy bytes are claimed with 32-bit atomics: pad to whole words
-        ok = ok && dev_alloc(ctx, &ctx->buf[b].cnt, size_t(ctx->Ctot) + 4);
-        ok = ok && dev_alloc(ctx, &ctx->buf[b].pid, slots);
+        // occupancy bytes are claimed with 32-bit atomics and bulk copies may
+        // read up to 15 bytes past a segment: pad every cell array
+        ok = ok && dev_alloc(ctx, &ctx->buf[b].cnt, size_t(ctx->Ctot) + kCellPad);
+        ok = ok && dev_alloc(ctx, &ctx->buf[b].pid, slots + kCellPad);
         if (ctx->fixed) {
             int2* p = nullptr;
-            ok = ok && dev_alloc(ctx, &p, slots);
+            ok = ok && dev_alloc(ctx, &p, slots + kCellPad);
             ctx->buf[b].pos = p;
         } else {
             double2* p = nullptr;
-            ok = ok && dev_alloc(ctx, &p, slots);
+            ok = ok && dev_alloc(ctx, &p, slots + kCellPad);
             ctx->buf[b].pos = p;
         }
     }
@@ -587,8 +616,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     cu = cu && cudaMemset(ctx->sweep_ctr, 0, sizeof(uint64_t) * size_t(R)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * size_t(2 * R)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
-    cu = cu && cudaMemset(ctx->buf[0].cnt, 0, size_t(ctx->Ctot) + 4) == cudaSuccess;
-    cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot) + 4) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->buf[0].cnt, 0, size_t(ctx->Ctot) + kCellPad) == cudaSuccess;
+    cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot) + kCellPad) == cudaSuccess;
     if (!cu) {
         free_ctx(ctx);
         return HD_ERR_CUDA;
@@ -914,7 +943,7 @@ void fill_header(const hd_ctx* ctx, CkHeader& h, std::vector<CkRep>& reps) {
     h.Ctot = ctx->Ctot;
     h.Ntot = ctx->Ntot;
     h.K = ctx->K;
-    h.sweep_kernel = ctx->fused ? 1 : 0;
+    h.sweep_kernel = 0;  // reserved: every sweep kernel runs the same chain on the same cell state
     reps.assign(size_t(ctx->R), CkRep{});
     for (int r = 0; r < ctx->R; ++r) {
         const Rep& s = ctx->reps[size_t(r)];
@@ -1072,7 +1101,7 @@ hd_status hd_restore(hd_ctx* ctx, const void* buf, size_t bytes) {
     HD_CK(ctx, cudaMemcpy(b.pid, p, slots * sizeof(int32_t), cudaMemcpyHostToDevice));
     p += slots * sizeof(int32_t);
     // the other generation's occupancy must be zero for the next scatter rebuild
-    HD_CK(ctx, cudaMemset(ctx->buf[ctx->cur ^ 1].cnt, 0, size_t(ctx->Ctot) + 4));
+    HD_CK(ctx, cudaMemset(ctx->buf[ctx->cur ^ 1].cnt, 0, size_t(ctx->Ctot) + kCellPad));
     HD_CK(ctx, cudaMemcpy(ctx->frame, p, sizeof(Frame) * size_t(ctx->R), cudaMemcpyHostToDevice));
     p += sizeof(Frame) * size_t(ctx->R);
     HD_CK(ctx, cudaMemcpy(ctx->sweep_ctr, p, sizeof(uint64_t) * size_t(ctx->R), cudaMemcpyHostToDevice));

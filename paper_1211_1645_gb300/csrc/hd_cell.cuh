@@ -195,15 +195,17 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
 // NT1: rep.nt is known to be 1 (one trial per occupied cell, the usual case
 // at liquid and solid densities), which lets the compiler keep every value's
 // live range to the single trial.
+// u0_in (fixed form, nullable): trial 0's block, when the caller has drawn it
+// already (to overlap the generator with its loads).
 template <bool FIX, int CAP, bool NT1 = false, class NbrClear>
 __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
-                                             NbrClear&& neighbours_clear) {
+                                             NbrClear&& neighbours_clear, const uint4* u0_in = nullptr) {
     uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
     // The fixed-point step uses two words of a trial block; the other two of
     // trial 0's block are the first two swap words, so a cell of up to three
     // occupants needs a single generator call.  The FP64 step uses all four.
     uint4 u0 = make_uint4(0, 0, 0, 0);
-    if constexpr (FIX) u0 = philox(sweep, 0u, cl, kTagTrial, rep.key0, rep.key1);
+    if constexpr (FIX) u0 = u0_in ? *u0_in : philox(sweep, 0u, cl, kTagTrial, rep.key0, rep.key1);
     if (n > 1) {
         uint4 w0, w1 = make_uint4(0, 0, 0, 0);
         if constexpr (FIX) {

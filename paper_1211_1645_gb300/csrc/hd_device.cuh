@@ -39,6 +39,12 @@ struct Rep {
     int32_t tiles_x;    // such tiles per row of cells, ceil(m / 32)
     uint32_t tx_mul;    // tx_mul, tx_sh: divide by tiles_x >= 2 with div_by
     int32_t tx_sh;
+    int32_t blk_seg;    // first block of the replica in half-row segment grids (one colour plane)
+    int32_t nseg;       // segments per half-row, ceil((m/2) / threads)
+    int32_t segw;       // half-columns per segment, ceil((m/2) / nseg)
+    uint32_t seg_mul;   // seg_mul, seg_sh: divide by nseg >= 2 with div_by
+    int32_t seg_sh;
+    int32_t pad_seg;
     double w, w_below;  // FP64 cell side and the largest double below it
     double L, delta;    // FP64 box side and maximum step (sigma units)
     double Lm;          // realised box side (fixed form: m W 2^-24) for g(r) and eta
@@ -137,7 +143,7 @@ __device__ __forceinline__ uint32_t row_part(const Rep& r, int cy) {
 }
 
 // Grids over all replicas: whole cells, active cells of one colour, tiles.
-enum GridKind { kGridCell = 0, kGridAct = 1, kGridTile = 2, kGridT32 = 3 };
+enum GridKind { kGridCell = 0, kGridAct = 1, kGridTile = 2, kGridT32 = 3, kGridSeg = 4 };
 
 // Replica owning block `blk`, given per-replica first blocks (ascending).
 template <int KIND>
@@ -148,6 +154,7 @@ __device__ __forceinline__ int find_rep(const Rep* __restrict__ reps, int R, int
         const int start = KIND == kGridAct    ? reps[mid].blk_act
                           : KIND == kGridTile ? reps[mid].blk_tile
                           : KIND == kGridT32  ? reps[mid].blk_t32
+                          : KIND == kGridSeg  ? reps[mid].blk_seg
                                               : reps[mid].blk_cell;
         if (start <= blk) lo = mid; else hi = mid - 1;
     }

@@ -29,6 +29,7 @@ struct LaunchCfg {
     int blocks_act;    // active-cell grid size (all replicas)
     int blocks_tile;   // fused-sweep tile grid size (all replicas)
     int blocks_t32;    // 32 x (threads / 32) cell-tile grid size (all replicas)
+    int blocks_seg;    // half-row segment grid size of one colour pass (all replicas)
     cudaStream_t stream;
 };
 
@@ -55,6 +56,9 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
                            int* err);
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters);
+// The colour pass with each block's neighbourhood staged by bulk copies (TMA).
+cudaError_t launch_pass_tma(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
+                            unsigned long long* counters, int* err);
 // One whole sweep (rebuild + four colour passes) per launch, staged in shared
 // memory by tiles of fused_tile(fixed, cap) cells per side.
 int fused_tile(bool fixed, int cap);

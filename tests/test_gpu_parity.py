@@ -46,7 +46,7 @@ def assert_same_state(g, o):
     assert np.array_equal(g.positions(), o.positions())
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
@@ -63,7 +63,7 @@ def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
     g.close()
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_chunk_boundary(hd, oracle_mod, form, kernel):
     """More sweeps in one call than one draw table holds (256)."""
@@ -173,7 +173,7 @@ def test_full_size_config2(hd, oracle_mod, form):
     assert np.array_equal(hist[0], o.histogram(50, 1e-3))
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
 def test_full_size_config3(hd, oracle_mod, form, kernel):
     """N = 1024^2 at eta = 0.716 (coexistence), the benchmark workload: whole
@@ -239,7 +239,7 @@ def test_overflow_rejected_on_set_positions(hd):
     assert e.value.status == HD_ERR_OVERFLOW
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "tma"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_graph_engine_series(hd, oracle_mod, form, kernel):
     """hd_run: graph-captured steps of 7 sweeps (odd, so both buffer parities
@@ -291,7 +291,7 @@ def test_graph_engine_batched(hd, oracle_mod, form):
         off += Ns[r]
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "tma"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_checkpoint_resume_bit_exact(hd, oracle_mod, form, kernel):
     """A chain checkpointed after 40 sweeps and restored into a fresh context
@@ -320,3 +320,20 @@ def test_restore_rejects_other_geometry(hd):
     assert e.value.status == HD_ERR_ARG
     with pytest.raises(HDError):
         g.restore(blob[:100])
+
+
+@pytest.mark.parametrize("threads", [32, 64, 256])
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_tma_pass_block_sizes(hd, oracle_mod, form, threads):
+    """The bulk-copy pass stages half-row segments whose width follows the
+    block size: one segment per half-row (m/2 <= threads), several, and
+    32-cell segments that wrap at both row ends; capacity-9 cells too."""
+    for N, eta, cell_min in ((1000, 0.70, 2.0), (4096, 0.60, 3.0)):
+        g = hd.HardDisks(N, eta, 0.15, 9, precision=form, sweep_kernel="tma", block_threads=threads,
+                         cell_min=cell_min)
+        o = oracle_mod.OracleChain(N, eta, 0.15, 9, form=form, cell_min=cell_min)
+        for n in (1, 7, 24):
+            g.sweep(n)
+            o.sweep(n)
+            assert_same_state(g, o)
+        g.close()
