@@ -11,7 +11,9 @@ correct statement of what the GPU library computes:
   global bond order psi_6 (Eq. 8).
 * this module - ctypes access to it, plus the g(r) normalisation (Eq. 2),
   the quartic contact extrapolation (Sec. II.C.1) and the contact-value
-  pressure (Eq. 4) in numpy.
+  pressure (Eq. 4) in numpy; the autocorrelation of the global psi_6 series
+  and its correlation time (Sec. III, Eq. 9, Table II); the coarse-grained
+  psi_6 field over square sampling areas (Sec. IV, Figs. 5-6).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library.
@@ -21,7 +23,10 @@ invariant; exact two-disk separation law and two-disk pressure; hard-disk
 virial series at low density; ideal-gas g(r) = (N-1)/N; exact synthetic
 quartic recovery; frame-change invariance; psi_6 of hand-built hexagonal
 shells and its rotation / reflection covariance; brute-force neighbour and
-pair enumeration.
+pair enumeration; the autocorrelation of constant and uniformly rotating
+series (exact), of a complex AR(1) process (rho^dt) and an exact exponential
+(tau); the coarse field of uniform psi_j, of one sampling area (= Psi_6),
+of disks on sampling-area edges, and against a per-area loop.
 """
 from __future__ import annotations
 
@@ -215,3 +220,58 @@ def contact_pressure(counts, N: int, L: float, dr: float, degree: int = 4) -> di
     bp_rho = 1.0 + 2.0 * eta * g0
     return {"g0": g0, "betaP_over_rho": bp_rho, "Pstar": bp_rho * 4.0 * N / (L * L), "eta": eta,
             "g": g, "r": r}
+
+
+def psi6_acf(psi, max_lag: int) -> np.ndarray:
+    """Eq. 9: C(dt) = <Psi_6(t) Psi_6*(t + dt)>_t / <|Psi_6|^2> of a series
+    Psi_6(t), t = 0 .. T-1, one entry per measurement.  The numerator averages
+    over the T - dt pairs the series holds, the denominator over all T
+    entries, so C(0) = 1.  Returns complex C(0 .. max_lag)."""
+    z = np.asarray(psi, dtype=np.complex128)
+    T = len(z)
+    if max_lag < 0 or max_lag >= T:
+        raise ValueError("need 0 <= max_lag < len(series)")
+    den = np.mean(z.real * z.real + z.imag * z.imag)
+    return np.array([np.mean(z[:T - d] * np.conj(z[d:])) / den for d in range(max_lag + 1)])
+
+
+def acf_tau(C, lag_lo: int, lag_hi: int) -> float:
+    """Correlation time from the purely exponential part C(dt) ~ exp(-dt / tau)
+    (Sec. III): the least-squares line through (dt, ln Re C(dt)) over
+    lag_lo <= dt <= lag_hi where Re C > 0; tau = -1 / slope, in the units of
+    dt.  NaN with fewer than two such lags or a slope >= 0."""
+    c = np.real(np.asarray(C))
+    d = np.arange(lag_lo, lag_hi + 1)
+    d = d[(d < len(c)) & (c[np.minimum(d, len(c) - 1)] > 0)]
+    if len(d) < 2:
+        return float("nan")
+    slope = np.polyfit(d.astype(np.float64), np.log(c[d]), 1)[0]
+    return float(-1.0 / slope) if slope < 0 else float("nan")
+
+
+def psi6_field(xy, psi_local, L: float, bins: int, LF: int | None = None) -> np.ndarray:
+    """Coarse-grained psi_6 (the sampling-area averages of Figs. 5-6): the
+    mean of psi_j over the disks whose centres lie in each of bins x bins
+    half-open squares of side L / bins, NaN where a square is empty.  Square
+    index floor(x bins / L) per axis; in the fixed-point form (LF = box side
+    in 2^-24 sigma units) the index is floor(X bins / LF) of the exact integer
+    coordinate X.  Returns complex [bins, bins] indexed [iy, ix]."""
+    xy = np.asarray(xy, dtype=np.float64)
+    psi = np.asarray(psi_local, dtype=np.complex128)
+    if LF is None:
+        ix = np.floor(xy[:, 0] * bins / L).astype(np.int64)
+        iy = np.floor(xy[:, 1] * bins / L).astype(np.int64)
+    else:
+        X = np.round(xy * FX_SCALE).astype(np.int64)
+        ix = (X[:, 0] * bins) // int(LF)
+        iy = (X[:, 1] * bins) // int(LF)
+    ix = np.minimum(ix, bins - 1)
+    iy = np.minimum(iy, bins - 1)
+    flat = iy * bins + ix
+    cnt = np.bincount(flat, minlength=bins * bins).astype(np.float64)
+    re = np.bincount(flat, weights=psi.real, minlength=bins * bins)
+    im = np.bincount(flat, weights=psi.imag, minlength=bins * bins)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out = (re + 1j * im) / cnt
+    out[cnt == 0] = np.nan + 1j * np.nan
+    return out.reshape(bins, bins)
