@@ -213,6 +213,41 @@ hd_status hd_series_reserve(hd_ctx *ctx, int64_t steps);
  * Synchronises. */
 hd_status hd_series(hd_ctx *ctx, int64_t *n_steps, double *out, int64_t max_steps);
 
+/*
+ * Autocorrelation of the global orientational order over the recorded series
+ * (Sec. III, Eq. 9): C(d) = <Psi_6(t) Psi_6*(t + d)>_t / <|Psi_6|^2>, the
+ * numerator averaged over the T - d pairs of a series of T entries, the
+ * denominator over all T, so C(0) = 1.  Lags d = 0 .. max_lag in units of
+ * recorded steps.  acf (host, caller-owned): [R][max_lag + 1][2] = (Re, Im).
+ * Synchronises.  Errors: HD_ERR_ARG if max_lag < 0 or max_lag >= T.
+ */
+hd_status hd_psi6_acf(hd_ctx *ctx, int64_t max_lag, double *acf);
+
+/*
+ * Correlation time from the purely exponential part of C (Sec. III, Table
+ * II): the least-squares line through (d, ln Re C(d)) over
+ * lag_lo <= d <= lag_hi where Re C(d) > 0; tau = -1 / slope, in recorded
+ * steps (multiply by sweeps per step and attempts per disk per sweep for
+ * Table II's displacements per disk).  tau (host, caller-owned): [R]; NaN
+ * where fewer than two lags qualify or the slope is not negative.
+ * Synchronises.  Errors: HD_ERR_ARG unless 0 <= lag_lo <= lag_hi < T.
+ */
+hd_status hd_psi6_tau(hd_ctx *ctx, int64_t lag_lo, int64_t lag_hi, double *tau);
+
+/*
+ * Coarse-grained psi_6 field of the current state (the sampling-area
+ * averages of Sec. IV, Figs. 5-6): the mean of psi_j (as hd_psi6) over the
+ * disks whose centres lie in each of bins x bins half-open squares of side
+ * L / bins; area index floor(x bins / L) per axis (fixed form:
+ * floor(X bins / LF) of the exact integer coordinate).  field (host,
+ * caller-owned): [R][bins][bins][2] = (Re, Im), indexed [r][iy][ix]; NaN for
+ * an empty area.  Sums are accumulated with atomics (summation order not
+ * fixed).  Synchronises.
+ * Errors: HD_ERR_ARG unless 1 <= bins <= 65536 and R bins^2 <= 2^28;
+ * HD_ERR_REACH as hd_psi6.
+ */
+hd_status hd_psi6_field(hd_ctx *ctx, int32_t bins, double *field);
+
 /* Forget the recorded steps (asynchronous). */
 hd_status hd_series_clear(hd_ctx *ctx);
 
@@ -288,7 +323,8 @@ typedef enum hd_kernel_class {
     HD_K_PSI6_REDUCE = 6,/* global Psi_6 reduction                            */
     HD_K_POSITIONS = 7,  /* cell frame to global positions                    */
     HD_K_SWEEP = 8,      /* one fused sweep (rebuild and four passes)         */
-    HD_KERNEL_CLASSES = 9
+    HD_K_ANALYSIS = 9,   /* Psi_6 autocorrelation, correlation time, field    */
+    HD_KERNEL_CLASSES = 10
 } hd_kernel_class;
 
 hd_status hd_profile(hd_ctx *ctx, int32_t enable);

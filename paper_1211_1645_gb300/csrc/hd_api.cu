@@ -40,6 +40,13 @@ struct hd_ctx {
     int threads = 128;
     bool fused = false;
     bool pass_tma = false;  // colour pass with bulk-copy (TMA) staging
+    // analysis scratch, grown on demand and freed with the context
+    double2* acf = nullptr;     // [R][max_lag + 1]
+    size_t acf_cap = 0;
+    double* tau = nullptr;      // [R]
+    double* field_acc = nullptr;  // [R][bins^2][3]
+    double2* field = nullptr;     // [R][bins^2]
+    size_t field_cap = 0;
     int tile = 48;
     double sigma = 1.0;
     std::vector<Rep> reps;
@@ -307,6 +314,10 @@ void free_ctx(hd_ctx* ctx) {
     drop_graphs(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->series) cudaFree(ctx->series);
+    if (ctx->acf) cudaFree(ctx->acf);
+    if (ctx->tau) cudaFree(ctx->tau);
+    if (ctx->field_acc) cudaFree(ctx->field_acc);
+    if (ctx->field) cudaFree(ctx->field);
     if (ctx->series_len) cudaFree(ctx->series_len);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
@@ -1143,3 +1154,90 @@ hd_status hd_kernel_times(hd_ctx* ctx, double* ms, int64_t* launches) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// The recorded series length (synchronises).
+hd_status series_length(hd_ctx* ctx, int64_t& T) {
+    T = 0;
+    if (!ctx->series) return HD_OK;
+    HD_CK(ctx, cudaMemcpyAsync(&T, ctx->series_len, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+// C[R][max_lag + 1] of the current series into ctx->acf.
+hd_status enqueue_acf(hd_ctx* ctx, int64_t T, int64_t max_lag) {
+    const size_t need = size_t(ctx->R) * size_t(max_lag + 1);
+    if (need > ctx->acf_cap) {
+        if (ctx->acf) cudaFree(ctx->acf);
+        ctx->acf = nullptr;
+        ctx->acf_cap = 0;
+        HD_CK(ctx, cudaMalloc(&ctx->acf, need * sizeof(double2)));
+        ctx->acf_cap = need;
+    }
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] { return hd::launch_acf(ctx->cfg(), ctx->series, T, max_lag, ctx->acf); }));
+    return HD_OK;
+}
+
+}  // namespace
+
+hd_status hd_psi6_acf(hd_ctx* ctx, int64_t max_lag, double* acf) {
+    if (!ctx || !acf || max_lag < 0) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    int64_t T = 0;
+    hd_status st = series_length(ctx, T);
+    if (st != HD_OK) return st;
+    if (max_lag >= T) return HD_ERR_ARG;
+    st = enqueue_acf(ctx, T, max_lag);
+    if (st != HD_OK) return st;
+    HD_CK(ctx, cudaMemcpyAsync(acf, ctx->acf, sizeof(double2) * size_t(ctx->R) * size_t(max_lag + 1),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+hd_status hd_psi6_tau(hd_ctx* ctx, int64_t lag_lo, int64_t lag_hi, double* tau) {
+    if (!ctx || !tau || lag_lo < 0 || lag_hi < lag_lo) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    int64_t T = 0;
+    hd_status st = series_length(ctx, T);
+    if (st != HD_OK) return st;
+    if (lag_hi >= T) return HD_ERR_ARG;
+    st = enqueue_acf(ctx, T, lag_hi);
+    if (st != HD_OK) return st;
+    if (!ctx->tau) HD_CK(ctx, cudaMalloc(&ctx->tau, sizeof(double) * size_t(ctx->R)));
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS,
+                      [&] { return hd::launch_acf_tau(ctx->cfg(), lag_hi, lag_lo, lag_hi, ctx->acf, ctx->tau); }));
+    HD_CK(ctx, cudaMemcpyAsync(tau, ctx->tau, sizeof(double) * size_t(ctx->R), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+hd_status hd_psi6_field(hd_ctx* ctx, int32_t bins, double* field) {
+    if (!ctx || !field || bins < 1 || bins > 65536) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const size_t need = size_t(ctx->R) * size_t(bins) * size_t(bins);
+    if (need > (size_t(1) << 28)) return HD_ERR_ARG;
+    if (need > ctx->field_cap) {
+        if (ctx->field_acc) cudaFree(ctx->field_acc);
+        if (ctx->field) cudaFree(ctx->field);
+        ctx->field_acc = nullptr;
+        ctx->field = nullptr;
+        ctx->field_cap = 0;
+        HD_CK(ctx, cudaMalloc(&ctx->field_acc, need * 3 * sizeof(double)));
+        HD_CK(ctx, cudaMalloc(&ctx->field, need * sizeof(double2)));
+        ctx->field_cap = need;
+    }
+    // global positions and local psi_6 of the current state, then the area means
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] {
+        return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], ctx->xy);
+    }));
+    HD_CK(ctx, enqueue_psi6(ctx, ctx->stream, true, false));
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] {
+        return hd::launch_field(ctx->cfg(), ctx->Ntot, bins, ctx->xy, ctx->psi_local, ctx->field_acc, ctx->field);
+    }));
+    HD_CK(ctx, cudaMemcpyAsync(field, ctx->field, need * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx);
+}

@@ -65,6 +65,14 @@ int fused_tile(bool fixed, int cap);
 cudaError_t launch_sweep_fused(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,
                                unsigned long long* counters, int* err);
 cudaError_t launch_positions(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy);
+// Psi_6 autocorrelation of the measurement series (series[T][R][4]) for lags
+// 0..max_lag into C[R][max_lag + 1], and the correlation time from it.
+cudaError_t launch_acf(const LaunchCfg& c, const double* series, int64_t T, int64_t max_lag, double2* C);
+cudaError_t launch_acf_tau(const LaunchCfg& c, int64_t max_lag, int64_t lag_lo, int64_t lag_hi, const double2* C,
+                           double* tau);
+// Coarse psi_6 field over bins x bins sampling areas per replica (acc: R bins^2 x 3 doubles of scratch).
+cudaError_t launch_field(const LaunchCfg& c, int64_t Ntot, int bins, const double* xy, const double2* psi,
+                         double* acc, double2* out);
 
 // Measurement.
 struct HistCfg {

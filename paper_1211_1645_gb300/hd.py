@@ -109,6 +109,9 @@ def load(path: str | None = None):
             "hd_checkpoint": (S, [P, P, c.c_size_t]),
             "hd_restore": (S, [P, P, c.c_size_t]),
             "hd_kernel_times": (S, [P, P, P]),
+            "hd_psi6_acf": (S, [P, c.c_int64, P]),
+            "hd_psi6_tau": (S, [P, c.c_int64, c.c_int64, P]),
+            "hd_psi6_field": (S, [P, c.c_int32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -296,11 +299,36 @@ def hd_series_clear(h):
     _check(load().hd_series_clear(h), "hd_series_clear")
 
 
-KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions", "sweep"]
+KERNEL_CLASSES = ["draws", "rebuild", "pass", "hist", "fit", "psi6", "psi6_reduce", "positions", "sweep",
+                  "analysis"]
 
 
 def hd_profile(h, enable: bool):
     _check(load().hd_profile(h, int(bool(enable))), "hd_profile")
+
+
+def hd_psi6_acf(h, max_lag: int):
+    """Eq. 9 autocorrelation of the recorded Psi_6 series: complex [R, max_lag + 1]."""
+    R = hd_replicas(h)
+    out = np.zeros((R, int(max_lag) + 1, 2), np.float64)
+    _check(load().hd_psi6_acf(h, int(max_lag), _ptr(out)), "hd_psi6_acf")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def hd_psi6_tau(h, lag_lo: int, lag_hi: int):
+    """Correlation time (in recorded steps) from the exponential part of C: [R]."""
+    R = hd_replicas(h)
+    out = np.zeros(R, np.float64)
+    _check(load().hd_psi6_tau(h, int(lag_lo), int(lag_hi), _ptr(out)), "hd_psi6_tau")
+    return out
+
+
+def hd_psi6_field(h, bins: int):
+    """Coarse-grained psi_6 over bins x bins sampling areas: complex [R, bins, bins] ([r, iy, ix])."""
+    R = hd_replicas(h)
+    out = np.zeros((R, int(bins), int(bins), 2), np.float64)
+    _check(load().hd_psi6_field(h, int(bins), _ptr(out)), "hd_psi6_field")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def hd_kernel_times(h):
@@ -389,3 +417,12 @@ class HardDisks:
 
     def kernel_times(self):
         return hd_kernel_times(self.h)
+
+    def psi6_acf(self, max_lag):
+        return hd_psi6_acf(self.h, max_lag)
+
+    def psi6_tau(self, lag_lo, lag_hi):
+        return hd_psi6_tau(self.h, lag_lo, lag_hi)
+
+    def psi6_field(self, bins):
+        return hd_psi6_field(self.h, bins)

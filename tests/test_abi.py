@@ -78,6 +78,9 @@ def test_null_context_calls(hdlib):
     assert lib.hd_positions(None, None) == b.HD_ERR_ARG
     assert lib.hd_destroy(None) == b.HD_OK
     assert lib.hd_replicas(None) == 0
+    assert lib.hd_psi6_acf(None, 3, None) == b.HD_ERR_ARG
+    assert lib.hd_psi6_tau(None, 1, 2, None) == b.HD_ERR_ARG
+    assert lib.hd_psi6_field(None, 4, None) == b.HD_ERR_ARG
 
 
 def test_no_cpu_fallback_without_gpu(hdlib):
