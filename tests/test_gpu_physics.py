@@ -69,3 +69,35 @@ def test_autotuner_picks_a_valid_fast_configuration(hd):
     assert best is not None and len(table) >= 3
     assert best["trial_moves_per_s"] == max(r["trial_moves_per_s"] for r in table)
     assert best["cell_min"] in (2.0, 2.4) and best["sweep_kernel"] in ("split", "fused")
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(__import__("os").environ.get("HD_SLOW") != "1",
+                    reason="about two minutes of GPU time: set HD_SLOW=1")
+def test_table1_mpmc_pressure_anchor(hd):
+    """Table I: N = 256^2 at eta = 0.698, MPMC P* = 9.17078 +- 4.5e-5 (8 runs
+    of 6e13 displacements).  Eight fixed-point replicas from the square
+    lattice, 10^6 sweeps of equilibration (Table II's tau at N = 512^2 is
+    8e5 displacements per disk), then 2 10^6 sweeps with the contact pressure
+    (100 bins of 10^-3 sigma, the paper's shell) every 1000 sweeps.  The
+    replica means must agree with the paper within three combined standard
+    errors (ours from the spread of the eight replica means)."""
+    import os
+    R, N, eta = 8, 256 * 256, 0.698
+    equil = int(os.environ.get("HD_SLOW_EQUIL", "1000000"))
+    prod = int(os.environ.get("HD_SLOW_PROD", "2000000"))
+    every = 1000
+    g = hd.HardDisks([N] * R, [eta] * R, [0.1] * R, [101 + r for r in range(R)], precision="fixed",
+                     hist_bins=100, hist_dr=1e-3)
+    g.run(equil // every, every, False)
+    g.series_reserve(prod // every + 8)
+    g.run(prod // every, every, True)
+    s = g.series()  # [T, R, 4]: beta P / rho first
+    etas = np.array([g.geometry(r)["eta"] for r in range(R)])
+    pstar = s[:, :, 0] * 4.0 * etas / np.pi  # P* = beta P (2 sigma)^2 = (beta P / rho) 4 eta / pi
+    means = pstar.mean(axis=0)
+    se = means.std(ddof=1) / np.sqrt(R)
+    want, want_se = 9.17078, 4.5e-5
+    print(f"P* = {means.mean():.5f} +- {se:.5f} (replica means {np.round(means, 4).tolist()}), paper {want} +- {want_se}")
+    assert abs(means.mean() - want) < 3.0 * np.hypot(se, want_se)
+    g.close()
