@@ -395,7 +395,9 @@ cudaError_t enqueue_pressure(hd_ctx* ctx, cudaStream_t s, bool capturing) {
     const hd::LaunchCfg c = ctx->cfg(s);
     cudaError_t e = cudaMemsetAsync(ctx->hist, 0, sizeof(unsigned long long) * size_t(ctx->R) * ctx->K, s);
     if (e != cudaSuccess) return e;
-    const hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF};
+    int halo = 0;
+    for (const hd::Rep& rep : ctx->reps) halo = std::max(halo, rep.hist_R);
+    const hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF, halo};
     e = launch(ctx, HD_K_HIST, [&] { return hd::launch_hist(c, h, ctx->buf[ctx->cur], ctx->hist); }, capturing);
     if (e != cudaSuccess) return e;
     return launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->hist, ctx->fit); }, capturing);

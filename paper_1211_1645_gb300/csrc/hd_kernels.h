@@ -79,6 +79,7 @@ struct HistCfg {
     int K;
     const double* edges;      // [K + 1] FP64 squared bin edges
     const long long* edgesF;  // [K + 1] fixed-point squared bin edges
+    int halo;                 // largest histogram reach (cells) over the replicas
 };
 cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist);
 cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res);

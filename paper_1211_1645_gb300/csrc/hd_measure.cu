@@ -23,10 +23,13 @@ constexpr int kMaxFitBins = 512;
 // comparing r^2 with squared bin edges; each pair is seen from its lower id.
 // One thread per cell scans the (2R+1)^2 stencil; counts gather in a shared
 // histogram and are flushed with one atomic per non-empty bin and block.
+// k_hist_global reads the stencil from global memory (any reach R);
+// k_hist_tile (reach up to kHistMaxHalo) first stages the block's 32 x rows
+// tile of cells and a halo of R cells in shared memory, like k_psi6.
 // ---------------------------------------------------------------------------
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
-k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ edges,
+k_hist_global(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ edges,
        const long long* __restrict__ edgesF, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
        const int32_t* __restrict__ pid, unsigned long long* __restrict__ hist) {
     extern __shared__ unsigned int s_bins[];
@@ -81,6 +84,97 @@ k_hist(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ ed
                             bin = lo;
                         }
                         atomicAdd(&s_bins[bin], 1u);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < K; b += blockDim.x)
+        if (s_bins[b]) atomicAdd(&hist[size_t(r) * K + b], (unsigned long long)s_bins[b]);
+}
+
+
+constexpr int kHistMaxHalo = 4;
+
+template <bool FIX, int CAP>
+__host__ __device__ constexpr size_t hist_stage_bytes(int rows, int halo, int K) {
+    return size_t(32 + 2 * halo) * size_t(rows + 2 * halo) * (CAP * (sizeof(P2<FIX>) + sizeof(int32_t)) + 1) + 16 +
+           size_t(K + 1) * 8 + size_t(K) * 4;
+}
+
+template <bool FIX, int CAP>
+__global__ void __launch_bounds__(256)
+k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ edges,
+            const long long* __restrict__ edgesF, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
+            const int32_t* __restrict__ pid, unsigned long long* __restrict__ hist, int H) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    pdl_begin();
+    const int r = find_rep<kGridT32>(reps, R, blockIdx.x);
+    const Rep& rep = reps[r];
+    const int m = rep.m;
+    const int rows = int(blockDim.x >> 5);
+    int X0, Y0;
+    tile32_origin(rep, uint32_t(blockIdx.x - rep.blk_t32), rows, X0, Y0);
+    const int SX = 32 + 2 * H, nS = SX * (rows + 2 * H);
+    P2<FIX>* s_pos = reinterpret_cast<P2<FIX>*>(s_raw);                  // [CAP][nS]
+    int32_t* s_id = reinterpret_cast<int32_t*>(s_pos + size_t(CAP) * nS);  // [CAP][nS]
+    uint8_t* s_n = reinterpret_cast<uint8_t*>(s_id + size_t(CAP) * nS);    // [nS]
+    using E = std::conditional_t<FIX, long long, double>;
+    E* s_edge = reinterpret_cast<E*>(s_raw + ((size_t(CAP) * nS * (sizeof(P2<FIX>) + 4) + nS + 15) & ~size_t(15)));
+    unsigned int* s_bins = reinterpret_cast<unsigned int*>(s_edge + (K + 1));
+    for (int b = threadIdx.x; b <= K; b += blockDim.x) {
+        if constexpr (FIX) s_edge[b] = edgesF[b];
+        else s_edge[b] = edges[b];
+        if (b < K) s_bins[b] = 0u;
+    }
+    for (int t = threadIdx.x; t < nS; t += blockDim.x) {
+        const int sy = t / SX, sx = t - sy * SX;
+        const uint32_t c = uint32_t(rep.coff) + row_part(rep, wrap_cell(Y0 - H + sy, m)) +
+                           col_part(rep, wrap_cell(X0 - H + sx, m));
+        const int n = min(int(cnt[c]), CAP);
+        s_n[t] = uint8_t(n);
+        for (int q = 0; q < n; ++q) {
+            s_pos[q * nS + t] = pos[size_t(q) * rep.stride32 + c];
+            s_id[q * nS + t] = pid[size_t(q) * rep.stride32 + c];
+        }
+    }
+    __syncthreads();
+    const int lx = int(threadIdx.x & 31u), ly = int(threadIdx.x >> 5);
+    if (X0 + lx < m && Y0 + ly < m) {
+        const int own = (ly + H) * SX + lx + H;
+        const int n = s_n[own];
+        const int RR = rep.hist_R;
+        const E lo_edge = s_edge[0], hi_edge = s_edge[K];
+        for (int k = 0; k < n; ++k) {
+            const P2<FIX> me = s_pos[k * nS + own];
+            const int32_t idme = s_id[k * nS + own];
+            for (int dcy = -RR; dcy <= RR; ++dcy) {
+                for (int dcx = -RR; dcx <= RR; ++dcx) {
+                    const int sc = own + dcy * SX + dcx;
+                    const int nn = s_n[sc];
+                    for (int q = 0; q < nn; ++q) {
+                        const int32_t idq = s_id[q * nS + sc];
+                        if (idq <= idme) continue;
+                        const P2<FIX> o = s_pos[q * nS + sc];
+                        E r2;
+                        if constexpr (FIX) {
+                            // |offset| < (RR + 1) W <= 5 W < 2^31
+                            const int32_t rx = (o.x + dcx * rep.W) - me.x;
+                            const int32_t ry = (o.y + dcy * rep.W) - me.y;
+                            r2 = int64_t(rx) * rx + int64_t(ry) * ry;
+                        } else {
+                            const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
+                            const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
+                            r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
+                        }
+                        if (r2 < lo_edge || r2 >= hi_edge) continue;
+                        int lo = 0, hi = K - 1;  // largest k with edge[k] <= r2
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_edge[mid] <= r2) lo = mid; else hi = mid - 1;
+                        }
+                        atomicAdd(&s_bins[lo], 1u);
                     }
                 }
             }
@@ -180,12 +274,15 @@ __global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K,
 template <bool FIX>
 struct Nbr {
     using Key = std::conditional_t<FIX, long long, double>;
+    // pair offsets: 32-bit in the fixed form (the ring search never reaches
+    // (RR + 1) W >= 2^31, so |r| < 2^31)
+    using Off = std::conditional_t<FIX, int32_t, double>;
     Key key[6];
     int32_t id[6];
-    Key rx[6], ry[6];
+    Off rx[6], ry[6];
     int n;
 
-    __device__ __forceinline__ void insert(Key k, int32_t i, Key x, Key y) {
+    __device__ __forceinline__ void insert(Key k, int32_t i, Off x, Off y) {
         if (n == 6 && !(k < key[5] || (k == key[5] && i < id[5]))) return;
         bool done = false;
         const int top = n < 6 ? n : 5;
@@ -222,9 +319,9 @@ __device__ __forceinline__ void scan_cell(const Rep& rep, const uint8_t* __restr
         if (idq == idme) continue;
         const P2<FIX> o = pos[q * rep.stride + nc];
         if constexpr (FIX) {
-            const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
-            const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
-            nb.insert(rx * rx + ry * ry, idq, rx, ry);
+            const int32_t rx = (o.x + dcx * rep.W) - me.x;
+            const int32_t ry = (o.y + dcy * rep.W) - me.y;
+            nb.insert(int64_t(rx) * rx + int64_t(ry) * ry, idq, rx, ry);
         } else {
             const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
             const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
@@ -336,9 +433,9 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                                 if (idq == idme) continue;
                                 const P2<FIX> o = s_pos[q * nS + sc];
                                 if constexpr (FIX) {
-                                    const long long rx = (static_cast<long long>(o.x) + static_cast<long long>(dcx) * rep.W) - me.x;
-                                    const long long ry = (static_cast<long long>(o.y) + static_cast<long long>(dcy) * rep.W) - me.y;
-                                    nb.insert(rx * rx + ry * ry, idq, rx, ry);
+                                    const int32_t rx = (o.x + dcx * rep.W) - me.x;
+                                    const int32_t ry = (o.y + dcy * rep.W) - me.y;
+                                    nb.insert(int64_t(rx) * rx + int64_t(ry) * ry, idq, rx, ry);
                                 } else {
                                     const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
                                     const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
@@ -369,8 +466,8 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                 float fr = 0.0f, fi = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    const float x = __fmul_rn(__ll2float_rn(nb.rx[q]), 0x1p-24f);
-                    const float y = __fmul_rn(__ll2float_rn(nb.ry[q]), 0x1p-24f);
+                    const float x = __fmul_rn(__int2float_rn(nb.rx[q]), 0x1p-24f);
+                    const float y = __fmul_rn(__int2float_rn(nb.ry[q]), 0x1p-24f);
                     const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y);
                     const float r2 = __fadd_rn(xx, yy);
                     const float c2 = __fsub_rn(xx, yy), s2 = __fmul_rn(__fmul_rn(x, y), 2.0f);
@@ -466,7 +563,18 @@ __global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_to
 // ---------------------------------------------------------------------------
 template <bool FIX, int CAP>
 static cudaError_t hist_t(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist) {
-    return launch_k(k_hist<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), size_t(h.K) * sizeof(unsigned int),
+    if (h.halo <= kHistMaxHalo) {
+        static std::once_flag attr_once;
+        std::call_once(attr_once, [] {
+            cudaFuncSetAttribute(k_hist_tile<FIX, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(hist_stage_bytes<FIX, CAP>(8, kHistMaxHalo, kMaxFitBins)));
+        });
+        return launch_k(k_hist_tile<FIX, CAP>, dim3(c.blocks_t32), dim3(c.threads),
+                        hist_stage_bytes<FIX, CAP>(c.threads / 32, h.halo, h.K), c.stream, c.reps, c.R, h.K, h.edges,
+                        h.edgesF, (const uint8_t*)cells.cnt, (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid,
+                        hist, h.halo);
+    }
+    return launch_k(k_hist_global<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), size_t(h.K) * sizeof(unsigned int),
                     c.stream, c.reps, c.R, h.K, h.edges, h.edgesF, (const uint8_t*)cells.cnt,
                     (const P2<FIX>*)cells.pos, (const int32_t*)cells.pid, hist);
 }
