@@ -108,7 +108,9 @@ struct hd_ctx {
         c.cap = cap;
         c.fixed = fixed;
         c.threads = threads;
-        c.nt1 = std::all_of(reps.begin(), reps.end(), [](const hd::Rep& r) { return r.nt == 1; });
+        c.ntc = 0;
+        for (int k : {1, 2})
+            if (std::all_of(reps.begin(), reps.end(), [k](const hd::Rep& r) { return r.nt == k; })) c.ntc = k;
         c.blocks_cell = blocks_cell;
         c.blocks_act = blocks_act;
         c.blocks_tile = blocks_tile;

@@ -192,12 +192,13 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
 // uniform in [-delta, delta]^2, rejected if it leaves the cell or comes
 // closer than 2 sigma to another occupant or to a disk of the eight
 // neighbouring cells (`neighbours_clear(np)`).  Updates P; returns accepts.
-// NT1: rep.nt is known to be 1 (one trial per occupied cell, the usual case
-// at liquid and solid densities), which lets the compiler keep every value's
-// live range to the single trial.
+// NTC > 0: rep.nt is known to be NTC at compile time (one trial per
+// occupied cell is the usual case at liquid and solid densities with the
+// smallest cells), which lets the compiler bound every value's live range;
+// NTC = 0 reads rep.nt.
 // u0_in (fixed form, nullable): trial 0's block, when the caller has drawn it
 // already (to overlap the generator with its loads).
-template <bool FIX, int CAP, bool NT1 = false, class NbrClear>
+template <bool FIX, int CAP, int NTC = 0, class NbrClear>
 __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
                                              NbrClear&& neighbours_clear, const uint4* u0_in = nullptr) {
     uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
@@ -237,7 +238,7 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
         }
     }
     uint32_t acc = 0;
-    const int nt = NT1 ? 1 : rep.nt;
+    const int nt = NTC > 0 ? NTC : rep.nt;
     for (int t = 0; t < nt; ++t) {
         const uint4 u = (FIX && t == 0) ? u0 : philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
         const int slot = int((order >> (4 * (n == 1 ? 0 : t % n))) & 0xFull);

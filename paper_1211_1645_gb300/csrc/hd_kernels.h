@@ -24,7 +24,7 @@ struct LaunchCfg {
     int cap;           // 4 or 9
     bool fixed;        // fixed-point form
     int threads;       // threads per block
-    bool nt1;          // every replica makes one trial per occupied cell and pass
+    int ntc;           // trials per occupied cell and pass when every replica has the same 1 or 2, else 0
     int blocks_cell;   // whole-cell grid size (all replicas)
     int blocks_act;    // active-cell grid size (all replicas)
     int blocks_tile;   // fused-sweep tile grid size (all replicas)

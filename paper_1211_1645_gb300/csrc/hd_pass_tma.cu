@@ -223,7 +223,7 @@ k_pass_tma(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table,
                 }
                 return ok;
             };
-            acc = try_cell<FIX, CAP, NT1>(rep, f.sweep, cl, P, n, neighbours_clear, FIX ? &u0 : nullptr);
+            acc = try_cell<FIX, CAP, NT1 ? 1 : 0>(rep, f.sweep, cl, P, n, neighbours_clear, FIX ? &u0 : nullptr);
             att = uint32_t(rep.nt);
             // written back in id order (the ids too, since the sort may have permuted them)
             if (acc > 0 || n > 1) {
@@ -257,7 +257,7 @@ static cudaError_t pass_tma_t(const LaunchCfg& c, const Frame* table, int j, int
 template <bool FIX, int CAP>
 static cudaError_t pass_tma_nt(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                                unsigned long long* counters, int* err) {
-    return c.nt1 ? pass_tma_t<FIX, CAP, true>(c, table, j, p, cells, counters, err)
+    return c.ntc == 1 ? pass_tma_t<FIX, CAP, true>(c, table, j, p, cells, counters, err)
                  : pass_tma_t<FIX, CAP, false>(c, table, j, p, cells, counters, err);
 }
 

@@ -74,6 +74,9 @@ __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__
 // With d = old shift - new shift in (-w, w), a coordinate u + d lies in
 // (-w, 2w), so a disk changes cell by at most one per axis.
 // ---------------------------------------------------------------------------
+// A thread handles two old cells, blockDim apart, and issues the loads of
+// both and then the slot claims of both before it waits on any, so the two
+// latency chains (loads, then claims, then stores) overlap.
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int j,
@@ -84,37 +87,79 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
     const int r = find_rep<kGridCell>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
     const int m = rep.m;
-    const uint32_t a = uint32_t(blockIdx.x - rep.blk_cell) * blockDim.x + threadIdx.x;
-    if (a >= uint32_t(m) * uint32_t(m)) return;
-    const uint32_t c = rep.coff + a;
-    const int n = occupancy<CAP>(cnt_o, c);
-    if (n == 0) return;
-    cnt_o[c] = 0;
-    int cx, cy;
-    cell_coords(rep, a, cx, cy);
-    const ShiftDelta<FIX> sd(table[size_t(r) * (kMaxChunk + 1) + j - 1], table[size_t(r) * (kMaxChunk + 1) + j]);
-    CellRegs<FIX, true> src;
-    load_cell<FIX, true, CAP>(cnt_o, pos_o, pid_o, rep.stride32, c, src);
-    bool over = false;
-    for (int k = 0; k < n; ++k) {
-        const P2<FIX> q = src.slot(k, pos_o, rep.stride32);
-        const int32_t id = src.slot_id(k, pid_o, rep.stride32);
-        int tcx, tcy;
-        P2<FIX> nq;
-        if constexpr (FIX) {
-            frame_change_fixed(sd.fx, rep.W, m, cx, q.x, tcx, nq.x);
-            frame_change_fixed(sd.fy, rep.W, m, cy, q.y, tcy, nq.y);
-        } else {
-            frame_change_fp64(sd.dx, rep.w, rep.w_below, m, cx, q.x, tcx, nq.x);
-            frame_change_fp64(sd.dy, rep.w, rep.w_below, m, cy, q.y, tcy, nq.y);
+    const uint32_t mm = uint32_t(m) * uint32_t(m);
+    const uint32_t a0 = uint32_t(blockIdx.x - rep.blk_cell) * (2u * blockDim.x) + threadIdx.x;
+    uint32_t c[2];
+    int n[2];
+    CellRegs<FIX, true> src[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t a = a0 + uint32_t(h) * blockDim.x;
+        c[h] = rep.coff + a;
+        n[h] = 0;
+        if (a < mm) {
+            load_cell<FIX, true, CAP>(cnt_o, pos_o, pid_o, rep.stride32, c[h], src[h]);
+            n[h] = src[h].n;
         }
-        const uint32_t di = rep.coff + row_part(rep, tcy) + col_part(rep, tcx);
-        const int s = claim_slot(cnt_n, di);
-        if (s < CAP) {
-            pos_n[size_t(s) * rep.stride32 + di] = nq;
-            pid_n[size_t(s) * rep.stride32 + di] = id;
+    }
+    if (n[0] == 0 && n[1] == 0) return;
+    const ShiftDelta<FIX> sd(table[size_t(r) * (kMaxChunk + 1) + j - 1], table[size_t(r) * (kMaxChunk + 1) + j]);
+    // destination and new offsets of the first kEagerSlots disks of both cells
+    uint32_t di[2][kEagerSlots];
+    P2<FIX> nq[2][kEagerSlots];
+    int cxy[2][2];
+    auto move = [&](const P2<FIX>& q, int cx, int cy, uint32_t& d, P2<FIX>& out) {
+        int tcx, tcy;
+        if constexpr (FIX) {
+            frame_change_fixed(sd.fx, rep.W, m, cx, q.x, tcx, out.x);
+            frame_change_fixed(sd.fy, rep.W, m, cy, q.y, tcy, out.y);
         } else {
-            over = true;
+            frame_change_fp64(sd.dx, rep.w, rep.w_below, m, cx, q.x, tcx, out.x);
+            frame_change_fp64(sd.dy, rep.w, rep.w_below, m, cy, q.y, tcy, out.y);
+        }
+        d = rep.coff + row_part(rep, tcy) + col_part(rep, tcx);
+    };
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (n[h] == 0) continue;
+        cnt_o[c[h]] = 0;  // leaves this buffer zeroed for the rebuild after next
+        cell_coords(rep, a0 + uint32_t(h) * blockDim.x, cxy[h][0], cxy[h][1]);
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k)
+            if (k < n[h]) move(src[h].s[k], cxy[h][0], cxy[h][1], di[h][k], nq[h][k]);
+    }
+    int slot[2][kEagerSlots];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k)
+            if (k < n[h]) slot[h][k] = claim_slot(cnt_n, di[h][k]);
+    bool over = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k) {
+            if (k < n[h]) {
+                if (slot[h][k] < CAP) {
+                    pos_n[size_t(slot[h][k]) * rep.stride32 + di[h][k]] = nq[h][k];
+                    pid_n[size_t(slot[h][k]) * rep.stride32 + di[h][k]] = src[h].id[k];
+                } else {
+                    over = true;
+                }
+            }
+        }
+        // crowded old cells (rare): the remaining disks one at a time
+        for (int k = kEagerSlots; k < n[h]; ++k) {
+            uint32_t d;
+            P2<FIX> q;
+            move(src[h].slot(k, pos_o, rep.stride32), cxy[h][0], cxy[h][1], d, q);
+            const int s2 = claim_slot(cnt_n, d);
+            if (s2 < CAP) {
+                pos_n[size_t(s2) * rep.stride32 + d] = q;
+                pid_n[size_t(s2) * rep.stride32 + d] = src[h].slot_id(k, pid_o, rep.stride32);
+            } else {
+                over = true;
+            }
         }
     }
     if (over) atomicOr(err, 1);
@@ -145,7 +190,7 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <bool FIX, int CAP, bool NT1>
+template <bool FIX, int CAP, int NTC>
 __global__ void __launch_bounds__(256)
 k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int j, int p,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
@@ -241,7 +286,7 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                 }
                 return ok;
             };
-            acc = try_cell<FIX, CAP, NT1>(rep, f.sweep, cl, P, n, neighbours_clear);
+            acc = try_cell<FIX, CAP, NTC>(rep, f.sweep, cl, P, n, neighbours_clear);
             att = uint32_t(rep.nt);
             // written back in id order (the ids too, since the sort may have permuted them)
             if (acc > 0 || n > 1) {
@@ -310,7 +355,7 @@ cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t*
 
 template <bool FIX, int CAP>
 static cudaError_t rebuild_t(const LaunchCfg& c, const Frame* table, int j, CellBufs a, CellBufs b, int* err) {
-    return launch_k(k_rebuild<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads), 0, c.stream, c.reps, c.R, table, j,
+    return launch_k(k_rebuild<FIX, CAP>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps, c.R, table, j,
                     a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt, (P2<FIX>*)b.pos, b.pid, err);
 }
 
@@ -319,24 +364,25 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
     return c.cap == 4 ? rebuild_t<false, 4>(c, table, j, from, to, err) : rebuild_t<false, 9>(c, table, j, from, to, err);
 }
 
-template <bool FIX, int CAP, bool NT1>
+template <bool FIX, int CAP, int NTC>
 static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                           unsigned long long* counters) {
     const size_t smem = pass_smem(FIX, c.threads);
     static std::once_flag attr_once;
     std::call_once(attr_once, [&] {
-        cudaFuncSetAttribute(k_pass<FIX, CAP, NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_pass<FIX, CAP, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(pass_smem(FIX, 256)));
     });
-    return launch_k(k_pass<FIX, CAP, NT1>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R, table,
+    return launch_k(k_pass<FIX, CAP, NTC>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R, table,
                     j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
 }
 
 template <bool FIX, int CAP>
 static cudaError_t pass_nt(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                            unsigned long long* counters) {
-    return c.nt1 ? pass_t<FIX, CAP, true>(c, table, j, p, cells, counters)
-                 : pass_t<FIX, CAP, false>(c, table, j, p, cells, counters);
+    // a compile-time count of two measured slower than the run-time loop, so only one is specialised
+    if (c.ntc == 1) return pass_t<FIX, CAP, 1>(c, table, j, p, cells, counters);
+    return pass_t<FIX, CAP, 0>(c, table, j, p, cells, counters);
 }
 
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,

@@ -20,6 +20,7 @@ CASES = {
     "ragged_N1000": dict(N=1000, eta=0.55, delta=0.25, seed=7),
     "triangular": dict(N=256, eta=0.72, delta=0.15, seed=3, lattice="triangular"),
     "three_trials": dict(N=400, eta=0.60, delta=0.2, seed=5, nt=3),
+    "two_trials_wide_cells": dict(N=1000, eta=0.716, delta=0.1, seed=6, cell_min=2.2),
     "cap9_cells": dict(N=300, eta=0.50, delta=0.4, seed=9, cell_min=3.0),
     "two_disks": dict(N=2, eta=2 * math.pi / 100, delta=1.0, seed=4),
 }
