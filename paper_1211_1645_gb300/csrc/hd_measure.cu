@@ -97,6 +97,37 @@ k_hist_global(const Rep* __restrict__ reps, int R, int K, const double* __restri
 
 constexpr int kHistMaxHalo = 4;
 
+// The disks of a block's 32 x rows tile of cells as one list, so that every
+// lane works on one disk (a lane per cell would make a warp repeat its scan
+// as many times as its most crowded cell holds disks).  Entry: staged cell
+// index << 4 | slot, in tile-cell order.  s_list holds blockDim * CAP
+// entries, s_warp one int per warp.  Returns the number of disks; every
+// thread of the block must call it, after the staging barrier.
+__device__ __forceinline__ int tile_disk_list(const uint8_t* s_n, int SX, int halo, int X0, int Y0, int m,
+                                              uint16_t* s_list, int* s_warp) {
+    const int lx = int(threadIdx.x & 31u), ly = int(threadIdx.x >> 5);
+    const int own = (ly + halo) * SX + lx + halo;
+    const int n = (X0 + lx < m && Y0 + ly < m) ? int(s_n[own]) : 0;
+    int v = n;  // inclusive warp scan of the occupancies
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lx >= o) v += u;
+    }
+    if (lx == 31) s_warp[ly] = v;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+        const int t = s_warp[w];
+        base += w < ly ? t : 0;
+        total += t;
+    }
+    const int off = base + v - n;
+    for (int q = 0; q < n; ++q) s_list[off + q] = uint16_t((own << 4) | q);
+    __syncthreads();
+    return total;
+}
+
 template <bool FIX, int CAP>
 __host__ __device__ constexpr size_t hist_stage_bytes(int rows, int halo, int K) {
     return size_t(32 + 2 * halo) * size_t(rows + 2 * halo) * (CAP * (sizeof(P2<FIX>) + sizeof(int32_t)) + 1) + 16 +
@@ -140,42 +171,41 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
         }
     }
     __syncthreads();
-    const int lx = int(threadIdx.x & 31u), ly = int(threadIdx.x >> 5);
-    if (X0 + lx < m && Y0 + ly < m) {
-        const int own = (ly + H) * SX + lx + H;
-        const int n = s_n[own];
-        const int RR = rep.hist_R;
-        const E lo_edge = s_edge[0], hi_edge = s_edge[K];
-        for (int k = 0; k < n; ++k) {
-            const P2<FIX> me = s_pos[k * nS + own];
-            const int32_t idme = s_id[k * nS + own];
-            for (int dcy = -RR; dcy <= RR; ++dcy) {
-                for (int dcx = -RR; dcx <= RR; ++dcx) {
-                    const int sc = own + dcy * SX + dcx;
-                    const int nn = s_n[sc];
-                    for (int q = 0; q < nn; ++q) {
-                        const int32_t idq = s_id[q * nS + sc];
-                        if (idq <= idme) continue;
-                        const P2<FIX> o = s_pos[q * nS + sc];
-                        E r2;
-                        if constexpr (FIX) {
-                            // |offset| < (RR + 1) W <= 5 W < 2^31
-                            const int32_t rx = (o.x + dcx * rep.W) - me.x;
-                            const int32_t ry = (o.y + dcy * rep.W) - me.y;
-                            r2 = int64_t(rx) * rx + int64_t(ry) * ry;
-                        } else {
-                            const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
-                            const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
-                            r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
-                        }
-                        if (r2 < lo_edge || r2 >= hi_edge) continue;
-                        int lo = 0, hi = K - 1;  // largest k with edge[k] <= r2
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_edge[mid] <= r2) lo = mid; else hi = mid - 1;
-                        }
-                        atomicAdd(&s_bins[lo], 1u);
+    __shared__ uint16_t s_list[256 * CAP];
+    __shared__ int s_warp[8];
+    const int D = tile_disk_list(s_n, SX, H, X0, Y0, m, s_list, s_warp);
+    const int RR = rep.hist_R;
+    const E lo_edge = s_edge[0], hi_edge = s_edge[K];
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        const int own = int(s_list[d] >> 4), k = int(s_list[d] & 15u);
+        const P2<FIX> me = s_pos[k * nS + own];
+        const int32_t idme = s_id[k * nS + own];
+        for (int dcy = -RR; dcy <= RR; ++dcy) {
+            for (int dcx = -RR; dcx <= RR; ++dcx) {
+                const int sc = own + dcy * SX + dcx;
+                const int nn = s_n[sc];
+                for (int q = 0; q < nn; ++q) {
+                    const int32_t idq = s_id[q * nS + sc];
+                    if (idq <= idme) continue;
+                    const P2<FIX> o = s_pos[q * nS + sc];
+                    E r2;
+                    if constexpr (FIX) {
+                        // |offset| < (RR + 1) W <= 5 W < 2^31
+                        const int32_t rx = (o.x + dcx * rep.W) - me.x;
+                        const int32_t ry = (o.y + dcy * rep.W) - me.y;
+                        r2 = int64_t(rx) * rx + int64_t(ry) * ry;
+                    } else {
+                        const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
+                        const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
+                        r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
                     }
+                    if (r2 < lo_edge || r2 >= hi_edge) continue;
+                    int lo = 0, hi = K - 1;  // largest k with edge[k] <= r2
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_edge[mid] <= r2) lo = mid; else hi = mid - 1;
+                    }
+                    atomicAdd(&s_bins[lo], 1u);
                 }
             }
         }
@@ -402,18 +432,20 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
     }
     __syncthreads();
 
+    __shared__ uint16_t s_list[256 * CAP];
+    __shared__ int s_warp[8];
+    const int D = tile_disk_list(s_n, kPsiSX, kPsiHalo, X0, Y0, m, s_list, s_warp);
     double sr = 0.0, si = 0.0;
-    const int lx = int(threadIdx.x & 31u), ly = int(threadIdx.x >> 5);
-    const int cx = X0 + lx, cy = Y0 + ly;
-    if (cx < m && cy < m) {
-        const int own = (ly + kPsiHalo) * kPsiSX + lx + kPsiHalo;
-        const int n = s_n[own];
-        int rmax = (m - 1) / 2;
-        if constexpr (FIX) {
-            const int lim = int((int64_t(1) << 31) / rep.W) - 1;
-            if (lim < rmax) rmax = lim;
-        }
-        for (int k = 0; k < n; ++k) {
+    int rmax = (m - 1) / 2;
+    if constexpr (FIX) {
+        const int lim = int((int64_t(1) << 31) / rep.W) - 1;
+        if (lim < rmax) rmax = lim;
+    }
+    {
+        for (int d = threadIdx.x; d < D; d += blockDim.x) {
+            const int own = int(s_list[d] >> 4), k = int(s_list[d] & 15u);
+            const int sy = own / kPsiSX;
+            const int cx = X0 + (own - sy * kPsiSX) - kPsiHalo, cy = Y0 + sy - kPsiHalo;
             const P2<FIX> me = s_pos[k * nS + own];
             const int32_t idme = s_id[k * nS + own];
             Nbr<FIX> nb;
