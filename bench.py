@@ -339,14 +339,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_sources_hash():
-    """First 16 hex digits of the sha256 of the CUDA sources (*.cu, *.cuh,
-    *.h of the library, in that order), as recorded beside ncu counters."""
+# CUDA sources each kernel class is compiled from (a recorded ncu traffic
+# figure stays valid while these are unchanged)
+KERNEL_SOURCES = {
+    "pass": ["hd_sweep.cu", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h"],
+    "rebuild": ["hd_sweep.cu", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h"],
+    "draws": ["hd_sweep.cu", "hd_device.cuh", "hd_kernels.h"],
+    "hist": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h"],
+    "psi6": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h"],
+}
+
+
+def kernel_sources_hash(kernel=None):
+    """First 16 hex digits of the sha256 of the CUDA sources a kernel class is
+    built from (all of them when the class is unknown or None), as recorded
+    beside ncu counters."""
     import glob
     import hashlib
     d = os.path.join(ROOT, "paper_1211_1645_gb300", "csrc")
-    files = (sorted(glob.glob(os.path.join(d, "*.cu"))) + sorted(glob.glob(os.path.join(d, "*.cuh")))
-             + sorted(glob.glob(os.path.join(d, "*.h"))))
+    if kernel in KERNEL_SOURCES:
+        files = [os.path.join(d, f) for f in KERNEL_SOURCES[kernel]]
+    else:
+        files = (sorted(glob.glob(os.path.join(d, "*.cu"))) + sorted(glob.glob(os.path.join(d, "*.cuh")))
+                 + sorted(glob.glob(os.path.join(d, "*.h"))))
     h = hashlib.sha256()
     for f in files:
         h.update(open(f, "rb").read())
@@ -358,7 +373,7 @@ def recorded_traffic(kernel):
     or None when no summary was taken on the current kernel sources."""
     import glob
     import re
-    want = kernel_sources_hash()
+    want = kernel_sources_hash(kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             mt = re.match(r"\s*traffic (\S+) bytes_per_launch=(\d+) sources=(\w+)", line)
