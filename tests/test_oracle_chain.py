@@ -125,3 +125,57 @@ def test_two_disk_separation_law(oracle_mod, form):
         want = (np.pi * R * R - 4 * np.pi) / (V - 4 * np.pi)
         mean, se = batch_se(r <= R)
         assert abs(mean - want) < 5 * se + 1e-3, (R, mean, want, se)
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_eight_disks_against_rejection_sampling(oracle_mod, form):
+    """Eight disks in a periodic 12 x 12 box (eta = 0.175) with 3-sigma cells
+    (two disks share a cell about half of the time, capacity-9 geometry) and
+    three trials per occupied cell: the chain's equilibrium distribution of
+    collective coordinates (the smallest pair distance and disk 0's nearest-
+    neighbour distance) must match exact samples of the uniform non-overlap
+    measure (Eq. 3), drawn by rejection from independent uniform positions.
+    This pins the stationary distribution with multi-occupied cells, their
+    shuffles, repeated trials of one cell and the frame shifts together.
+    (Any position-independent choice of the moving disk leaves that
+    distribution unchanged: every single move satisfies detailed balance.)"""
+    L, N = 12.0, 8
+    eta = N * np.pi / (L * L)
+    o = oracle_mod.OracleChain(N, eta, 0.8, 2024, form=form, nt=3, cell_min=3.0)
+    geo = o.geometry()
+    assert geo["m"] == 4 and geo["nt"] == 3 and abs(geo["L"] - L) < 1e-6
+    iu = np.triu_indices(N, 1)
+
+    def stats(xy):  # xy [..., N, 2] -> (min pair distance, disk 0's nearest neighbour)
+        d = xy[..., :, None, :] - xy[..., None, :, :]
+        d -= L * np.round(d / L)
+        r = np.hypot(d[..., 0], d[..., 1])
+        return r[..., iu[0], iu[1]].min(axis=-1), r[..., 0, 1:].min(axis=-1)
+
+    o.sweep(500)
+    nsamp = 25000
+    mc = np.empty((nsamp, 2))
+    multi = 0
+    for t in range(nsamp):
+        o.sweep(2)
+        mc[t] = stats(o.positions())
+        cells, _, _ = o.frame()
+        multi += len({tuple(c) for c in cells}) < N
+    assert multi > 0.3 * nsamp  # cells with two disks are common
+
+    rng = np.random.default_rng(77)
+    ref = []
+    while sum(len(a) for a in ref) < 60000:
+        xy = rng.uniform(0.0, L, (100000, N, 2))
+        d = xy[:, :, None, :] - xy[:, None, :, :]
+        d -= L * np.round(d / L)
+        r = np.hypot(d[..., 0], d[..., 1])
+        ok = r[:, iu[0], iu[1]].min(axis=1) >= 2.0
+        ref.append(np.stack(stats(xy[ok]), axis=1))
+    ref = np.concatenate(ref)
+    for col, cuts in ((0, (2.1, 2.25, 2.5, 3.0)), (1, (2.5, 3.0, 3.5, 4.0))):
+        for R in cuts:
+            want = float(np.mean(ref[:, col] <= R))
+            want_se = np.sqrt(want * (1 - want) / len(ref))
+            mean, se = batch_se(mc[:, col] <= R)
+            assert abs(mean - want) < 5 * np.hypot(se, want_se) + 2e-3, (col, R, mean, want, se)
