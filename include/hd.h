@@ -171,11 +171,13 @@ hd_status hd_positions(hd_ctx *ctx, double *xy);
 hd_status hd_positions_device(hd_ctx *ctx, double *xy_device);
 
 /*
- * Replace all positions (host, [2 * sum N_r], periodic images allowed).  The
- * cell frame is reset to shift zero; counters and the sweep index are kept.
- * Overlapping input is accepted (measurements then count it); the fixed form
- * rounds to the 2^-24 sigma grid.  Synchronises.
- * Errors: HD_ERR_OVERFLOW if a cell would hold more disks than its capacity.
+ * Replace all positions (host, [2 * sum N_r], periodic images allowed; pinned
+ * memory gives the fastest copy).  The positions are copied to the device
+ * and binned there into the unshifted cell frame; counters and the sweep
+ * index are kept.  Overlapping input is accepted (measurements then count
+ * it); the fixed form rounds to the 2^-24 sigma grid.  Synchronises.
+ * Errors (the previous state is kept): HD_ERR_OVERFLOW if a cell would hold
+ * more disks than its capacity; HD_ERR_ARG for a non-finite coordinate.
  */
 hd_status hd_set_positions(hd_ctx *ctx, const double *xy);
 

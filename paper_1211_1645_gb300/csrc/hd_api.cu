@@ -10,6 +10,7 @@
 
 #include "hd.h"
 #include "hd_kernels.h"
+#include "hd_bin.h"
 
 using hd::CellBufs;
 using hd::Frame;
@@ -762,33 +763,32 @@ hd_status hd_positions(hd_ctx* ctx, double* xy) {
 hd_status hd_set_positions(hd_ctx* ctx, const double* xy) {
     if (!ctx || !xy) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
-    HostCells h;
-    host_cells_init(ctx, h);
-    for (int r = 0; r < ctx->R; ++r) {
-        const Rep& rep = ctx->reps[size_t(r)];
-        for (int64_t k = 0; k < rep.N; ++k) {
-            const double px = xy[2 * (rep.id_off + k)] / ctx->sigma;
-            const double py = xy[2 * (rep.id_off + k) + 1] / ctx->sigma;
-            if (!std::isfinite(px) || !std::isfinite(py)) return HD_ERR_ARG;
-            double x = 0.0, y = 0.0;
-            int64_t X = 0, Y = 0;
-            if (ctx->fixed) {
-                X = std::llround(px * kFx) % rep.LF;
-                Y = std::llround(py * kFx) % rep.LF;
-                if (X < 0) X += rep.LF;
-                if (Y < 0) Y += rep.LF;
-            } else {
-                x = std::fmod(px, rep.L);
-                y = std::fmod(py, rep.L);
-                if (x < 0.0) x += rep.L;
-                if (y < 0.0) y += rep.L;
-                if (x >= rep.L) x = 0.0;
-                if (y >= rep.L) y = 0.0;
-            }
-            if (!bin_disk(ctx, rep, h, k, x, y, X, Y)) return HD_ERR_OVERFLOW;
-        }
+    // upload, then bin on the device into the other generation; switch to it
+    // only when every disk found a slot, so a rejected input changes nothing
+    const hd::LaunchCfg c = ctx->cfg();
+    const size_t cnt_bytes = size_t(ctx->Ctot) + kCellPad;
+    CellBufs& to = ctx->buf[ctx->cur ^ 1];
+    HD_CK(ctx, cudaMemcpyAsync(ctx->xy, xy, sizeof(double) * 2 * size_t(ctx->Ntot), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    HD_CK(ctx, cudaMemsetAsync(to.cnt, 0, cnt_bytes, ctx->stream));
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] { return hd::launch_bin(c, ctx->Ntot, ctx->sigma, ctx->xy, to, ctx->err); }));
+    int flag = 0;
+    HD_CK(ctx, cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const int bad = flag & (hd::kErrBinOverflow | hd::kErrBinInput);
+    if (bad) {
+        HD_CK(ctx, cudaMemsetAsync(to.cnt, 0, cnt_bytes, ctx->stream));  // the rebuild expects it cleared
+        const int keep = flag & ~bad;
+        HD_CK(ctx, cudaMemcpyAsync(ctx->err, &keep, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return (bad & hd::kErrBinInput) ? HD_ERR_ARG : HD_ERR_OVERFLOW;
     }
-    return upload_cells(ctx, h);
+    ctx->cur ^= 1;
+    // the generation left behind must be cleared for the next rebuild; the frame is unshifted
+    HD_CK(ctx, cudaMemsetAsync(ctx->buf[ctx->cur ^ 1].cnt, 0, cnt_bytes, ctx->stream));
+    HD_CK(ctx, cudaMemsetAsync(ctx->frame, 0, sizeof(Frame) * size_t(ctx->R), ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_flags(ctx);
 }
 
 hd_status hd_stats(hd_ctx* ctx, uint64_t* attempts, uint64_t* accepts) {
