@@ -178,10 +178,12 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
         static_assert(kFxDiam2 == (int64_t(1) << 50), "the high-word test assumes (2 sigma)^2 = 2^50");
         return uint32_t(d2 >> 32) >= (1u << 18);
     } else {
-        const double offx = ox < 0 ? -rep.w : (ox > 0 ? rep.w : 0.0);
-        const double offy = oy < 0 ? -rep.w : (oy > 0 ? rep.w : 0.0);
-        const double rx = __dsub_rn(__dadd_rn(q.x, offx), np.x);
-        const double ry = __dsub_rn(__dadd_rn(q.y, offy), np.y);
+        // (q + 0) is q itself for the non-negative cell offsets, so a zero
+        // cell difference skips that addition (an FP64 operation saved)
+        const double qx = ox == 0 ? q.x : __dadd_rn(q.x, ox < 0 ? -rep.w : rep.w);
+        const double qy = oy == 0 ? q.y : __dadd_rn(q.y, oy < 0 ? -rep.w : rep.w);
+        const double rx = __dsub_rn(qx, np.x);
+        const double ry = __dsub_rn(qy, np.y);
         return !(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) < 4.0);
     }
 }
