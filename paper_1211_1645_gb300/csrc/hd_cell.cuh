@@ -264,9 +264,16 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
         // them all), without branches: a slot that is not an occupant, or the
         // moving disk itself, masks its own result.  A move outside the cell
         // keeps every difference within int32 (|dx| < 3W).
+        if constexpr (FIX) {
 #pragma unroll
-        for (int q = 0; q < CAP; ++q)
-            ok &= pair_clear<FIX>(P[q], 0, 0, np, rep) | (q >= n) | (q == slot);
+            for (int q = 0; q < CAP; ++q)
+                ok &= pair_clear<FIX>(P[q], 0, 0, np, rep) | (q >= n) | (q == slot);
+        } else {
+            // FP64 arithmetic bounds the FP64 form: a warp skips a test no lane needs
+#pragma unroll
+            for (int q = 0; q < CAP; ++q)
+                if (ok && q < n && q != slot) ok = pair_clear<FIX>(P[q], 0, 0, np, rep);
+        }
         if (FIX || ok) ok &= neighbours_clear(np);  // the FP64 form loads neighbours lazily: skip when rejected
         if (ok) {
 #pragma unroll
