@@ -13,7 +13,9 @@ correct statement of what the GPU library computes:
   the quartic contact extrapolation (Sec. II.C.1) and the contact-value
   pressure (Eq. 4) in numpy; the autocorrelation of the global psi_6 series
   and its correlation time (Sec. III, Eq. 9, Table II); the coarse-grained
-  psi_6 field over square sampling areas (Sec. IV, Figs. 5-6).
+  psi_6 field over square sampling areas (Sec. IV, Figs. 5-6); the structure
+  factor, the positional order chi_j and the positional correlation function
+  (Sec. IV.C, Eqs. 10-12).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library.
@@ -275,3 +277,62 @@ def psi6_field(xy, psi_local, L: float, bins: int, LF: int | None = None) -> np.
         out = (re + 1j * im) / cnt
     out[cnt == 0] = np.nan + 1j * np.nan
     return out.reshape(bins, bins)
+
+
+def structure_factor(xy, hk, L: float) -> np.ndarray:
+    """Eq. 10: S(q) = (1/N) sum_{n,m} exp(i q (x_n - x_m)) = |sum_n exp(i q x_n)|^2 / N
+    at the box-periodic wave vectors q = 2 pi (h, k) / L, hk [nq, 2] integers."""
+    xy = np.asarray(xy, dtype=np.float64)
+    q = 2.0 * np.pi * np.asarray(hk, dtype=np.float64) / L
+    amp = np.exp(1j * (xy @ q.T)).sum(axis=0)
+    return (amp.real ** 2 + amp.imag ** 2) / len(xy)
+
+
+def q0_window(psi6_global: complex, eta: float, L: float, half_width: int) -> np.ndarray:
+    """Candidate wave vectors for q_0 (Sec. IV.C): the box's reciprocal grid
+    points within +-half_width of the first-shell reciprocal vector of a
+    triangular lattice of the same density (|q| = 4 pi / (a sqrt 3), area per
+    disk sqrt(3) a^2 / 2) whose bonds follow the global orientation
+    (angle arg(Psi_6) / 6), i.e. at that angle + 30 degrees.  The paper leaves
+    q_0 to the maximum of S near this point because vacancies and other
+    defects stretch the effective lattice constant.  Returns hk [nq, 2]."""
+    rho = eta / np.pi
+    a = np.sqrt(2.0 / (np.sqrt(3.0) * rho))
+    qmag = 4.0 * np.pi / (a * np.sqrt(3.0))
+    th = np.angle(psi6_global) / 6.0 + np.pi / 6.0
+    hc = int(np.rint(qmag * np.cos(th) * L / (2.0 * np.pi)))
+    kc = int(np.rint(qmag * np.sin(th) * L / (2.0 * np.pi)))
+    d = np.arange(-half_width, half_width + 1)
+    H, K = np.meshgrid(hc + d, kc + d, indexing="ij")
+    return np.stack([H.ravel(), K.ravel()], axis=1)
+
+
+def positional_q0(xy, hk_window, L: float):
+    """q_0 = the candidate of largest S (first in window order on ties)."""
+    S = structure_factor(xy, hk_window, L)
+    i = int(np.argmax(S))
+    return np.asarray(hk_window[i]), float(S[i])
+
+
+def positional_chi(xy, hk0, L: float) -> np.ndarray:
+    """Eq. 11: chi_j = exp(i q_0 . x_j), q_0 = 2 pi hk0 / L."""
+    q = 2.0 * np.pi * np.asarray(hk0, dtype=np.float64) / L
+    return np.exp(1j * (np.asarray(xy, dtype=np.float64) @ q))
+
+
+def positional_corr(xy, hk0, L: float, r):
+    """Eq. 12: C(r) = < exp(i q_0 (x_n - x_m)) > over the ordered pairs n != m
+    whose minimum-image separation lies in [r - sigma, r + sigma] (sigma = 1),
+    for every r of `r`; NaN where no pair qualifies.  Brute force."""
+    xy = np.asarray(xy, dtype=np.float64)
+    chi = positional_chi(xy, hk0, L)
+    d = xy[:, None, :] - xy[None, :, :]
+    d -= L * np.round(d / L)
+    dist = np.hypot(d[..., 0], d[..., 1])
+    prod = chi[:, None] * np.conj(chi[None, :])
+    np.fill_diagonal(dist, -10.0)
+    out = np.empty(len(r), complex)
+    for i, rr in enumerate(r):
+        sel = (dist >= rr - 1.0) & (dist <= rr + 1.0)
+        out[i] = prod[sel].mean() if sel.any() else np.nan + 1j * np.nan
+    return out
