@@ -250,6 +250,52 @@ hd_status hd_psi6_tau(hd_ctx *ctx, int64_t lag_lo, int64_t lag_hi, double *tau);
  */
 hd_status hd_psi6_field(hd_ctx *ctx, int32_t bins, double *field);
 
+/*
+ * Structure factor (Sec. IV.C, Eq. 10) of the current state:
+ * S(q) = (1/N) |sum_n exp(i q . x_n)|^2 at the box-periodic wave vectors
+ * q = 2 pi (h, k) / L.  hk (host): [R][nq][2] integers (h, k) per replica;
+ * S (host, caller-owned): [R][nq].  Phases are reduced to turn fractions
+ * (exactly, in integers, in the fixed form) before the sine and cosine.
+ * Synchronises.  Errors: HD_ERR_ARG unless 1 <= nq <= 65536 (and the
+ * partial sums fit the scratch bound).
+ */
+hd_status hd_structure_factor(hd_ctx *ctx, int32_t nq, const int32_t *hk, double *S);
+
+/*
+ * q_0 of the positional order (Sec. IV.C): the wave vector of largest S
+ * among the (2 half_width + 1)^2 box-grid points around the first-shell
+ * reciprocal vector of a triangular lattice of the same density
+ * (|q| = 4 pi / (a sqrt 3), area per disk sqrt(3) a^2 / 2), oriented by the
+ * global Psi_6 (angle arg(Psi_6) / 6 + 30 degrees); the paper leaves q_0 to
+ * the maximum of S because defects stretch the effective lattice constant.
+ * hk0 (host): [R][2] = (h, k); S0 (host, nullable): [R].  Synchronises.
+ * Errors: HD_ERR_ARG unless 0 <= half_width <= 64; HD_ERR_REACH as hd_psi6.
+ */
+hd_status hd_positional_q0(hd_ctx *ctx, int32_t half_width, int32_t *hk0, double *S0);
+
+/*
+ * Positional order field (Sec. IV.C, Eq. 11): chi_j = exp(i q_0 . x_j) with
+ * q_0 = 2 pi hk0[r] / L, averaged over bins x bins sampling areas as in
+ * hd_psi6_field.  hk0 (host): [R][2]; field (host, caller-owned):
+ * [R][bins][bins][2], NaN for an empty area.  Synchronises.
+ * Errors: HD_ERR_ARG unless 1 <= bins <= 65536 and R bins^2 <= 2^28.
+ */
+hd_status hd_positional_field(hd_ctx *ctx, const int32_t *hk0, int32_t bins, double *field);
+
+/*
+ * Positional correlation function (Sec. IV.C, Eq. 12):
+ * C(r_k) = < exp(i q_0 . (x_n - x_m)) > over the ordered pairs n != m whose
+ * minimum-image separation d (from the global positions,
+ * d = x_m - x_n - L rint((x_m - x_n) / L), d^2 = dx dx + dy dy) satisfies
+ * max(r_k - sigma, 0)^2 <= d^2 <= (r_k + sigma)^2, at r_k = (k + 1) dr,
+ * k = 0 .. nr - 1 (dr in the caller's length unit).  hk0 (host): [R][2];
+ * C (host, caller-owned): [R][nr][2] = (Re, Im), NaN where no pair
+ * qualifies.  Sums are accumulated with atomics.  Synchronises.
+ * Errors: HD_ERR_ARG unless 1 <= nr <= 1024 and dr > 0; HD_ERR_REACH if the
+ * cells within reach of r_nr + sigma would wrap around the box.
+ */
+hd_status hd_positional_corr(hd_ctx *ctx, const int32_t *hk0, int32_t nr, double dr, double *C);
+
 /* Forget the recorded steps (asynchronous). */
 hd_status hd_series_clear(hd_ctx *ctx);
 

@@ -323,16 +323,20 @@ def positional_chi(xy, hk0, L: float) -> np.ndarray:
 def positional_corr(xy, hk0, L: float, r):
     """Eq. 12: C(r) = < exp(i q_0 (x_n - x_m)) > over the ordered pairs n != m
     whose minimum-image separation lies in [r - sigma, r + sigma] (sigma = 1),
-    for every r of `r`; NaN where no pair qualifies.  Brute force."""
+    for every r of `r`; NaN where no pair qualifies.  Brute force.  The
+    window test is lo^2 <= d^2 <= (r + 1)^2 with lo = max(r - 1, 0) and
+    d^2 = dx dx + dy dy of the minimum-image difference d = x_m - x_n -
+    L rint((x_m - x_n) / L) of the global positions, in that operation order."""
     xy = np.asarray(xy, dtype=np.float64)
     chi = positional_chi(xy, hk0, L)
-    d = xy[:, None, :] - xy[None, :, :]
-    d -= L * np.round(d / L)
-    dist = np.hypot(d[..., 0], d[..., 1])
+    d = xy[None, :, :] - xy[:, None, :]  # [n, m] = x_m - x_n
+    d = d - L * np.rint(d / L)
+    d2 = d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]
     prod = chi[:, None] * np.conj(chi[None, :])
-    np.fill_diagonal(dist, -10.0)
+    np.fill_diagonal(d2, -10.0)
     out = np.empty(len(r), complex)
     for i, rr in enumerate(r):
-        sel = (dist >= rr - 1.0) & (dist <= rr + 1.0)
+        lo = max(rr - 1.0, 0.0)
+        sel = (d2 >= lo * lo) & (d2 <= (rr + 1.0) * (rr + 1.0))
         out[i] = prod[sel].mean() if sel.any() else np.nan + 1j * np.nan
     return out

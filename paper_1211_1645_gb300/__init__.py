@@ -11,14 +11,15 @@ binding of that library (``hd``) and its build step (``build``).
 from . import build
 from .hd import (HD_FIXED32, HD_FP64, HDError, HardDisks, hd_batch_init, hd_checkpoint, hd_destroy,
                  hd_get_geometry, hd_init, hd_kernel_times, hd_positions, hd_positions_device, hd_pressure, hd_profile,
-                 hd_psi6, hd_psi6_acf, hd_psi6_field, hd_psi6_tau, hd_replicas, hd_restore, hd_run, hd_series,
-                 hd_series_clear, hd_series_reserve, hd_set_delta, hd_set_positions, hd_set_stream, hd_stats, hd_sweep,
-                 hd_tune_delta, load, make_opts)
+                 hd_positional_corr, hd_positional_field, hd_positional_q0, hd_psi6, hd_psi6_acf, hd_psi6_field, hd_psi6_tau, hd_replicas, hd_restore, hd_run, hd_series,
+                 hd_series_clear, hd_series_reserve, hd_set_delta, hd_set_positions, hd_set_stream, hd_stats,
+                 hd_structure_factor, hd_sweep, hd_tune_delta, load, make_opts)
 
 __all__ = [
     "build", "load", "make_opts", "HardDisks", "HDError", "HD_FP64", "HD_FIXED32", "hd_init", "hd_batch_init",
     "hd_destroy", "hd_sweep", "hd_pressure", "hd_psi6", "hd_positions", "hd_positions_device",
     "hd_set_positions", "hd_stats", "hd_get_geometry", "hd_replicas", "hd_set_stream", "hd_run", "hd_series",
     "hd_series_reserve", "hd_series_clear", "hd_profile", "hd_kernel_times", "hd_checkpoint", "hd_restore",
-    "hd_set_delta", "hd_tune_delta", "hd_psi6_acf", "hd_psi6_tau", "hd_psi6_field",
+    "hd_set_delta", "hd_tune_delta", "hd_psi6_acf", "hd_psi6_tau", "hd_psi6_field", "hd_structure_factor",
+    "hd_positional_q0", "hd_positional_field", "hd_positional_corr",
 ]

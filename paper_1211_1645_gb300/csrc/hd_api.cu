@@ -10,6 +10,7 @@
 
 #include "hd.h"
 #include "hd_kernels.h"
+#include "hd_analysis.h"
 #include "hd_bin.h"
 
 using hd::CellBufs;
@@ -48,6 +49,15 @@ struct hd_ctx {
     double* field_acc = nullptr;  // [R][bins^2][3]
     double2* field = nullptr;     // [R][bins^2]
     size_t field_cap = 0;
+    int2* sq_hk = nullptr;          // [R][nq] wave vectors
+    double2* sq_part = nullptr;     // [R][disk blocks][nq] partial amplitudes
+    double* sq_S = nullptr;         // [R][nq]
+    int* sq_best = nullptr;         // [R]
+    size_t sq_cap = 0, sq_S_cap = 0, sq_part_cap = 0;  // capacities of sq_hk, sq_S, sq_part
+    double2* chi = nullptr;         // [Ntot] positional order by disk id
+    double* corr_acc = nullptr;     // [R][nr][3]
+    double2* corr = nullptr;        // [R][nr]
+    size_t corr_cap = 0;
     int tile = 48;
     double sigma = 1.0;
     std::vector<Rep> reps;
@@ -321,6 +331,9 @@ void free_ctx(hd_ctx* ctx) {
     if (ctx->tau) cudaFree(ctx->tau);
     if (ctx->field_acc) cudaFree(ctx->field_acc);
     if (ctx->field) cudaFree(ctx->field);
+    for (void* q : {(void*)ctx->sq_hk, (void*)ctx->sq_part, (void*)ctx->sq_S, (void*)ctx->sq_best, (void*)ctx->chi,
+                    (void*)ctx->corr_acc, (void*)ctx->corr})
+        if (q) cudaFree(q);
     if (ctx->series_len) cudaFree(ctx->series_len);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
@@ -1244,4 +1257,154 @@ hd_status hd_psi6_field(hd_ctx* ctx, int32_t bins, double* field) {
     HD_CK(ctx, cudaMemcpyAsync(field, ctx->field, need * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
     return check_flags(ctx);
+}
+
+namespace {
+
+template <class T>
+hd_status grow(hd_ctx* ctx, T*& p, size_t& cap, size_t need) {
+    if (need <= cap && p) return HD_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    HD_CK(ctx, cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(T)));
+    cap = need;
+    return HD_OK;
+}
+
+// S at the wave vectors already in ctx->sq_hk ([R][nq]); positions refreshed first.
+hd_status enqueue_sq(hd_ctx* ctx, int nq) {
+    std::vector<int64_t> Ns;
+    for (const Rep& r : ctx->reps) Ns.push_back(r.N);
+    const int nbx = hd::sq_disk_blocks(Ns);
+    const size_t need = size_t(ctx->R) * size_t(nbx) * size_t(nq);
+    if (need > (size_t(1) << 27)) return HD_ERR_ARG;
+    hd_status st = grow(ctx, ctx->sq_part, ctx->sq_part_cap, need);
+    if (st != HD_OK) return st;
+    st = grow(ctx, ctx->sq_S, ctx->sq_S_cap, size_t(ctx->R) * nq);
+    if (st != HD_OK) return st;
+    if (!ctx->sq_best) HD_CK(ctx, cudaMalloc(&ctx->sq_best, sizeof(int) * size_t(ctx->R)));
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] {
+        return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], ctx->xy);
+    }));
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] {
+        return hd::launch_sq(ctx->cfg(), nq, ctx->sq_hk, ctx->xy, nbx, ctx->sq_part, ctx->sq_S, ctx->sq_best);
+    }));
+    return HD_OK;
+}
+
+}  // namespace
+
+hd_status hd_structure_factor(hd_ctx* ctx, int32_t nq, const int32_t* hk, double* S) {
+    if (!ctx || !hk || !S || nq < 1 || nq > 65536) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    hd_status st = grow(ctx, ctx->sq_hk, ctx->sq_cap, size_t(ctx->R) * nq);
+    if (st != HD_OK) return st;
+    HD_CK(ctx, cudaMemcpyAsync(ctx->sq_hk, hk, sizeof(int2) * size_t(ctx->R) * nq, cudaMemcpyHostToDevice, ctx->stream));
+    st = enqueue_sq(ctx, nq);
+    if (st != HD_OK) return st;
+    HD_CK(ctx, cudaMemcpyAsync(S, ctx->sq_S, sizeof(double) * size_t(ctx->R) * nq, cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+hd_status hd_positional_q0(hd_ctx* ctx, int32_t half_width, int32_t* hk0, double* S0) {
+    if (!ctx || !hk0 || half_width < 0 || half_width > 64) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const int w = 2 * half_width + 1, nq = w * w;
+    hd_status st = grow(ctx, ctx->sq_hk, ctx->sq_cap, size_t(ctx->R) * nq);
+    if (st != HD_OK) return st;
+    HD_CK(ctx, enqueue_psi6(ctx, ctx->stream, false, false));  // Psi_6 orients the window
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] { return hd::launch_q0_window(ctx->cfg(), half_width, ctx->psi_res, ctx->sq_hk); }));
+    st = enqueue_sq(ctx, nq);
+    if (st != HD_OK) return st;
+    std::vector<int2> win(size_t(ctx->R) * nq);
+    std::vector<int> best(size_t(ctx->R));
+    std::vector<double> Sv(size_t(ctx->R) * nq);
+    HD_CK(ctx, cudaMemcpyAsync(win.data(), ctx->sq_hk, sizeof(int2) * win.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaMemcpyAsync(best.data(), ctx->sq_best, sizeof(int) * best.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaMemcpyAsync(Sv.data(), ctx->sq_S, sizeof(double) * Sv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const hd_status f = check_flags(ctx);
+    if (f != HD_OK) return f;
+    for (int r = 0; r < ctx->R; ++r) {
+        const size_t i = size_t(r) * nq + size_t(best[size_t(r)]);
+        hk0[2 * r] = win[i].x;
+        hk0[2 * r + 1] = win[i].y;
+        if (S0) S0[r] = Sv[i];
+    }
+    return HD_OK;
+}
+
+namespace {
+
+// chi_j of the current state for hk0[R][2] into ctx->chi (positions refreshed first).
+hd_status enqueue_chi(hd_ctx* ctx, const int32_t* hk0) {
+    if (!ctx->chi) HD_CK(ctx, cudaMalloc(&ctx->chi, sizeof(double2) * size_t(std::max<int64_t>(ctx->Ntot, 1))));
+    hd_status st = grow(ctx, ctx->sq_hk, ctx->sq_cap, size_t(ctx->R));
+    if (st != HD_OK) return st;
+    HD_CK(ctx, cudaMemcpyAsync(ctx->sq_hk, hk0, sizeof(int2) * size_t(ctx->R), cudaMemcpyHostToDevice, ctx->stream));
+    HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] {
+        return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], ctx->xy);
+    }));
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] { return hd::launch_chi(ctx->cfg(), ctx->Ntot, ctx->sq_hk, ctx->xy, ctx->chi); }));
+    return HD_OK;
+}
+
+}  // namespace
+
+hd_status hd_positional_field(hd_ctx* ctx, const int32_t* hk0, int32_t bins, double* field) {
+    if (!ctx || !hk0 || !field || bins < 1 || bins > 65536) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    const size_t need = size_t(ctx->R) * size_t(bins) * size_t(bins);
+    if (need > (size_t(1) << 28)) return HD_ERR_ARG;
+    hd_status st = enqueue_chi(ctx, hk0);
+    if (st != HD_OK) return st;
+    if (need > ctx->field_cap) {
+        if (ctx->field_acc) cudaFree(ctx->field_acc);
+        if (ctx->field) cudaFree(ctx->field);
+        ctx->field_acc = nullptr;
+        ctx->field = nullptr;
+        ctx->field_cap = 0;
+        HD_CK(ctx, cudaMalloc(&ctx->field_acc, need * 3 * sizeof(double)));
+        HD_CK(ctx, cudaMalloc(&ctx->field, need * sizeof(double2)));
+        ctx->field_cap = need;
+    }
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] {
+        return hd::launch_field(ctx->cfg(), ctx->Ntot, bins, ctx->xy, ctx->chi, ctx->field_acc, ctx->field);
+    }));
+    HD_CK(ctx, cudaMemcpyAsync(field, ctx->field, need * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
+}
+
+hd_status hd_positional_corr(hd_ctx* ctx, const int32_t* hk0, int32_t nr, double dr, double* C) {
+    if (!ctx || !hk0 || !C || nr < 1 || nr > 1024 || !(dr > 0.0)) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    // cell reach that holds every pair within the largest window, r_nr + 1 (sigma units)
+    const double rmax = double(nr) * dr + 1.0;
+    int reach = 0;
+    for (const Rep& r : ctx->reps) reach = std::max(reach, int(std::ceil(rmax / r.w)) + 1);
+    for (const Rep& r : ctx->reps)
+        if (2 * reach + 1 > r.m) return HD_ERR_REACH;
+    hd_status st = enqueue_chi(ctx, hk0);
+    if (st != HD_OK) return st;
+    const size_t need = size_t(ctx->R) * size_t(nr);
+    if (need > ctx->corr_cap) {
+        if (ctx->corr_acc) cudaFree(ctx->corr_acc);
+        if (ctx->corr) cudaFree(ctx->corr);
+        ctx->corr_acc = nullptr;
+        ctx->corr = nullptr;
+        ctx->corr_cap = 0;
+        HD_CK(ctx, cudaMalloc(&ctx->corr_acc, need * 3 * sizeof(double)));
+        HD_CK(ctx, cudaMalloc(&ctx->corr, need * sizeof(double2)));
+        ctx->corr_cap = need;
+    }
+    HD_CK(ctx, launch(ctx, HD_K_ANALYSIS, [&] {
+        return hd::launch_poscorr(ctx->cfg(), ctx->buf[ctx->cur], ctx->xy, ctx->chi, nr, dr / ctx->sigma, reach,
+                                  ctx->corr_acc, ctx->corr);
+    }));
+    HD_CK(ctx, cudaMemcpyAsync(C, ctx->corr, need * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return HD_OK;
 }

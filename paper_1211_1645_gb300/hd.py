@@ -112,6 +112,10 @@ def load(path: str | None = None):
             "hd_psi6_acf": (S, [P, c.c_int64, P]),
             "hd_psi6_tau": (S, [P, c.c_int64, c.c_int64, P]),
             "hd_psi6_field": (S, [P, c.c_int32, P]),
+            "hd_structure_factor": (S, [P, c.c_int32, P, P]),
+            "hd_positional_q0": (S, [P, c.c_int32, P, P]),
+            "hd_positional_field": (S, [P, P, c.c_int32, P]),
+            "hd_positional_corr": (S, [P, P, c.c_int32, c.c_double, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -331,6 +335,45 @@ def hd_psi6_field(h, bins: int):
     return out[..., 0] + 1j * out[..., 1]
 
 
+def hd_structure_factor(h, hk):
+    """Eq. 10 at the wave vectors 2 pi (h, k) / L: hk [R, nq, 2] (or [nq, 2] for every replica) -> S [R, nq]."""
+    R = hd_replicas(h)
+    hk = np.asarray(hk, np.int32)
+    if hk.ndim == 2:
+        hk = np.broadcast_to(hk, (R,) + hk.shape)
+    hk = np.ascontiguousarray(hk, np.int32)
+    out = np.zeros((R, hk.shape[1]), np.float64)
+    _check(load().hd_structure_factor(h, int(hk.shape[1]), _ptr(hk), _ptr(out)), "hd_structure_factor")
+    return out
+
+
+def hd_positional_q0(h, half_width: int = 3):
+    """q_0 = (h, k) of largest S around the first reciprocal shell: ([R, 2] ints, S0 [R])."""
+    R = hd_replicas(h)
+    hk0 = np.zeros((R, 2), np.int32)
+    S0 = np.zeros(R, np.float64)
+    _check(load().hd_positional_q0(h, int(half_width), _ptr(hk0), _ptr(S0)), "hd_positional_q0")
+    return hk0, S0
+
+
+def hd_positional_field(h, hk0, bins: int):
+    """Mean of chi_j = exp(i q_0 . x_j) over bins x bins areas: complex [R, bins, bins]."""
+    R = hd_replicas(h)
+    hk0 = np.ascontiguousarray(np.broadcast_to(np.asarray(hk0, np.int32), (R, 2)), np.int32)
+    out = np.zeros((R, int(bins), int(bins), 2), np.float64)
+    _check(load().hd_positional_field(h, _ptr(hk0), int(bins), _ptr(out)), "hd_positional_field")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def hd_positional_corr(h, hk0, nr: int, dr: float):
+    """Eq. 12 at r_k = (k + 1) dr: complex [R, nr]."""
+    R = hd_replicas(h)
+    hk0 = np.ascontiguousarray(np.broadcast_to(np.asarray(hk0, np.int32), (R, 2)), np.int32)
+    out = np.zeros((R, int(nr), 2), np.float64)
+    _check(load().hd_positional_corr(h, _ptr(hk0), int(nr), float(dr), _ptr(out)), "hd_positional_corr")
+    return out[..., 0] + 1j * out[..., 1]
+
+
 def hd_kernel_times(h):
     """{class: (total device ms or 0 when not profiled, launches)}."""
     ms = np.zeros(len(KERNEL_CLASSES), np.float64)
@@ -426,3 +469,15 @@ class HardDisks:
 
     def psi6_field(self, bins):
         return hd_psi6_field(self.h, bins)
+
+    def structure_factor(self, hk):
+        return hd_structure_factor(self.h, hk)
+
+    def positional_q0(self, half_width=3):
+        return hd_positional_q0(self.h, half_width)
+
+    def positional_field(self, hk0, bins):
+        return hd_positional_field(self.h, hk0, bins)
+
+    def positional_corr(self, hk0, nr, dr):
+        return hd_positional_corr(self.h, hk0, nr, dr)

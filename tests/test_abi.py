@@ -81,6 +81,10 @@ def test_null_context_calls(hdlib):
     assert lib.hd_psi6_acf(None, 3, None) == b.HD_ERR_ARG
     assert lib.hd_psi6_tau(None, 1, 2, None) == b.HD_ERR_ARG
     assert lib.hd_psi6_field(None, 4, None) == b.HD_ERR_ARG
+    assert lib.hd_structure_factor(None, 1, None, None) == b.HD_ERR_ARG
+    assert lib.hd_positional_q0(None, 1, None, None) == b.HD_ERR_ARG
+    assert lib.hd_positional_field(None, None, 4, None) == b.HD_ERR_ARG
+    assert lib.hd_positional_corr(None, None, 4, 0.5, None) == b.HD_ERR_ARG
 
 
 def test_no_cpu_fallback_without_gpu(hdlib):
