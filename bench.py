@@ -304,7 +304,7 @@ def time_e2e(args, form, rank, steps):
 
 
 def algorithmic_bytes(kernel, N, m, form):
-    """Minimum memory traffic of one launch of `kernel` (see DESIGN.md).
+    """Minimum memory traffic of one launch of `kernel`.
 
     sweep (fused): the state (coordinates, id, cell occupancy) read once and
     written once.  pass: every occupancy byte and every coordinate pair read

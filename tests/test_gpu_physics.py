@@ -17,7 +17,8 @@ def hd():
 
 @pytest.mark.parametrize("form,N", [("fixed", 65536), ("fp64", 16384)])
 def test_tune_delta_reaches_target_acceptance(hd, form, N):
-    """Config 2 asks for delta tuned to ~30% acceptance; after tuning the
+    """The N = 256^2, eta = 0.708 liquid is run with delta tuned to ~30%
+    acceptance; after tuning the
     acceptance of later sweeps is within 0.03 of the target."""
     g = hd.HardDisks(N, 0.708, 0.1, 3, precision=form)
     g.sweep(100)
