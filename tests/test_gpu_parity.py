@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 PSI_TOL = {"fp64": 1e-12, "fixed": 2.5e-7}
 
 CASES = {
-    "config1_N256": dict(N=256, eta=0.70, delta=0.1, seed=1),
+    "square_N256": dict(N=256, eta=0.70, delta=0.1, seed=1),
     "ragged_N1000": dict(N=1000, eta=0.55, delta=0.25, seed=7),
     "triangular": dict(N=256, eta=0.72, delta=0.15, seed=3, lattice="triangular"),
     "three_trials": dict(N=400, eta=0.60, delta=0.2, seed=5, nt=3),
@@ -92,7 +92,7 @@ def test_pressure(hd, oracle_mod, form, K, dr):
 
 
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
-@pytest.mark.parametrize("case", ["config1_N256", "ragged_N1000", "cap9_cells"])
+@pytest.mark.parametrize("case", ["square_N256", "ragged_N1000", "cap9_cells"])
 def test_psi6(hd, oracle_mod, form, case):
     g, o = make_pair(hd, oracle_mod, form, **CASES[case])
     g.sweep(40)
@@ -164,7 +164,7 @@ def test_batched_replicas(hd, oracle_mod, form):
 
 
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
-def test_full_size_config2(hd, oracle_mod, form):
+def test_full_size_N65536_liquid(hd, oracle_mod, form):
     """N = 256^2 at eta = 0.708 (liquid side), whole state compared."""
     g, o = make_pair(hd, oracle_mod, form, 65536, 0.708, 0.1, 2)
     g.sweep(20)
@@ -176,7 +176,7 @@ def test_full_size_config2(hd, oracle_mod, form):
 
 @pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
-def test_full_size_config3(hd, oracle_mod, form, kernel):
+def test_full_size_N1048576_coexistence(hd, oracle_mod, form, kernel):
     """N = 1024^2 at eta = 0.716 (coexistence), the benchmark workload: whole
     state, histogram and every psi_j compared after three sweeps."""
     N = 1024 * 1024
@@ -195,7 +195,7 @@ def test_full_size_config3(hd, oracle_mod, form, kernel):
     assert abs(glob[0] - rglob) <= 1e-12
 
 
-def test_full_size_config5(hd, oracle_mod):
+def test_full_size_N4194304_shifted_rows(hd, oracle_mod):
     """N = 2048^2 at eta = 0.720 from the shifted-row lattice, fixed point."""
     N = 2048 * 2048
     g, o = make_pair(hd, oracle_mod, "fixed", N, 0.720, 0.1, 5, lattice="triangular")
