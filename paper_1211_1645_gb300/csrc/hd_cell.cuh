@@ -200,9 +200,38 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
 // NTC = 0 reads rep.nt.
 // u0_in (fixed form, nullable): trial 0's block, when the caller has drawn it
 // already (to overlap the generator with its loads).
-template <bool FIX, int CAP, int NTC = 0, class NbrClear>
-__device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
-                                             NbrClear&& neighbours_clear, const uint4* u0_in = nullptr) {
+// A cell's occupants as try_cell sees them: in registers (slot q of a
+// register array, a run-time q picked by compile-time selects) or in shared
+// memory (any slot read directly).
+template <bool FIX, int CAP>
+struct RegCell {
+    P2<FIX> (&P)[CAP];
+    __device__ __forceinline__ P2<FIX> operator[](int q) const { return P[q]; }
+    __device__ __forceinline__ P2<FIX> pick(int slot) const {
+        P2<FIX> me = P[0];
+#pragma unroll
+        for (int q = 1; q < CAP; ++q)
+            if (q == slot) me = P[q];
+        return me;
+    }
+    __device__ __forceinline__ void put(int slot, const P2<FIX>& v) const {
+#pragma unroll
+        for (int q = 0; q < CAP; ++q)
+            if (q == slot) P[q] = v;
+    }
+};
+
+template <bool FIX>
+struct SmemCell {
+    P2<FIX>* P;  // shared memory, slot q at P[q]
+    __device__ __forceinline__ P2<FIX> operator[](int q) const { return P[q]; }
+    __device__ __forceinline__ P2<FIX> pick(int slot) const { return P[slot]; }
+    __device__ __forceinline__ void put(int slot, const P2<FIX>& v) const { P[slot] = v; }
+};
+
+template <bool FIX, int CAP, int NTC = 0, class Cell, class NbrClear>
+__device__ __forceinline__ uint32_t try_cell_in(const Rep& rep, uint32_t sweep, uint32_t cl, const Cell& P, int n,
+                                                NbrClear&& neighbours_clear, const uint4* u0_in = nullptr) {
     uint64_t order = 0xFEDCBA9876543210ull;  // position -> slot, one nibble each
     // The fixed-point step uses two words of a trial block; the other two of
     // trial 0's block are the first two swap words, so a cell of up to three
@@ -244,10 +273,7 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
     for (int t = 0; t < nt; ++t) {
         const uint4 u = (FIX && t == 0) ? u0 : philox(sweep, uint32_t(t), cl, kTagTrial, rep.key0, rep.key1);
         const int slot = int((order >> (4 * (n == 1 ? 0 : t % n))) & 0xFull);
-        P2<FIX> me = P[0];
-#pragma unroll
-        for (int q = 1; q < CAP; ++q)
-            if (q == slot) me = P[q];
+        const P2<FIX> me = P.pick(slot);
         P2<FIX> np;
         bool ok;
         if constexpr (FIX) {
@@ -276,13 +302,18 @@ __device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uin
         }
         if (FIX || ok) ok &= neighbours_clear(np);  // the FP64 form loads neighbours lazily: skip when rejected
         if (ok) {
-#pragma unroll
-            for (int q = 0; q < CAP; ++q)
-                if (q == slot) P[q] = np;
+            P.put(slot, np);
             ++acc;
         }
     }
     return acc;
+}
+
+// try_cell_in on occupants held in a register array.
+template <bool FIX, int CAP, int NTC = 0, class NbrClear>
+__device__ __forceinline__ uint32_t try_cell(const Rep& rep, uint32_t sweep, uint32_t cl, P2<FIX> (&P)[CAP], int n,
+                                             NbrClear&& neighbours_clear, const uint4* u0_in = nullptr) {
+    return try_cell_in<FIX, CAP, NTC>(rep, sweep, cl, RegCell<FIX, CAP>{P}, n, neighbours_clear, u0_in);
 }
 
 // Sum two per-thread counters over the block and add them to counters[2r],

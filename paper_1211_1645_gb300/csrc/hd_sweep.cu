@@ -181,8 +181,11 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
 // shared-memory wavefronts.
 constexpr int kNbrStride = 17;
 
-size_t pass_smem(bool fixed, int threads) {
-    return fixed ? size_t(threads) * kNbrStride * sizeof(int2) : 0;
+// ... followed by each thread's area for the occupants of a crowded cell
+// (more than kEagerSlots disks): CAP positions and CAP ids.
+template <bool FIX, int CAP>
+constexpr size_t pass_smem(int threads) {
+    return (FIX ? size_t(threads) * kNbrStride * sizeof(int2) : 0) + size_t(threads) * CAP * (sizeof(P2<FIX>) + 4);
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
@@ -195,7 +198,10 @@ __global__ void __launch_bounds__(256)
 k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int j, int p,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
     pdl_begin();
-    extern __shared__ int2 s_nbr[];
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    int2* s_nbr = reinterpret_cast<int2*>(s_raw);
+    P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + (FIX ? size_t(blockDim.x) * kNbrStride * sizeof(int2) : 0));
+    int32_t* s_crowd_id = reinterpret_cast<int32_t*>(s_crowd + size_t(blockDim.x) * CAP);
     const int r = find_rep<kGridAct>(reps, R, blockIdx.x);
     const Rep rep = reps[r];
     const int m = rep.m, hm = rep.hm;
@@ -235,16 +241,6 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
         load_cell<FIX, true, CAP>(cnt, pos, pid, rep.stride32, cell, own);
         const int n = own.n;
         if (n > 0) {
-            // occupants in ascending id: the base order of the shuffle
-            P2<FIX> P[CAP];
-            int32_t ids[CAP];
-#pragma unroll
-            for (int q = 0; q < CAP; ++q) {
-                const bool live = q < kEagerSlots || q < n;
-                P[q] = live ? own.slot(q, pos, rep.stride32) : P2<FIX>{};
-                ids[q] = live ? own.slot_id(q, pid, rep.stride32) : 0;
-            }
-            if (n > 1) sort_by_id<FIX, CAP>(P, ids, n);
             auto neighbours_clear = [&](const P2<FIX>& np) {
                 bool ok = true;
                 if constexpr (FIX) {
@@ -286,19 +282,47 @@ k_pass(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, int
                 }
                 return ok;
             };
-            acc = try_cell<FIX, CAP, NTC>(rep, f.sweep, cl, P, n, neighbours_clear);
+            if (n <= kEagerSlots) {
+                // the usual cell: its occupants in registers, in ascending id
+                // (the base order of the shuffle)
+                P2<FIX> P[kEagerSlots] = {own.s[0], own.s[1]};
+                int32_t ids[kEagerSlots] = {own.id[0], own.id[1]};
+                if (n > 1) sort_by_id<FIX, kEagerSlots>(P, ids, n);
+                acc = try_cell<FIX, kEagerSlots, NTC>(rep, f.sweep, cl, P, n, neighbours_clear);
+                // written back in id order (the ids too, since the sort may have permuted them)
+                if (acc > 0 || n > 1) {
+#pragma unroll
+                    for (int q = 0; q < kEagerSlots; ++q)
+                        if (q < n) pos[size_t(q) * rep.stride32 + cell] = P[q];
+                }
+                if (n > 1) {
+#pragma unroll
+                    for (int q = 0; q < kEagerSlots; ++q)
+                        if (q < n) pid[size_t(q) * rep.stride32 + cell] = ids[q];
+                }
+            } else {
+                // a crowded cell (rare): its occupants in this thread's shared
+                // area, so that the registers stay sized for two
+                P2<FIX>* sp = s_crowd + threadIdx.x * CAP;
+                int32_t* si = s_crowd_id + threadIdx.x * CAP;
+                for (int q = 0; q < n; ++q) {
+                    P2<FIX> v = own.slot(q, pos, rep.stride32);
+                    int32_t id = own.slot_id(q, pid, rep.stride32);
+                    int k = q;
+                    for (; k > 0 && si[k - 1] > id; --k) {
+                        sp[k] = sp[k - 1];
+                        si[k] = si[k - 1];
+                    }
+                    sp[k] = v;
+                    si[k] = id;
+                }
+                acc = try_cell_in<FIX, CAP, NTC>(rep, f.sweep, cl, SmemCell<FIX>{sp}, n, neighbours_clear);
+                for (int q = 0; q < n; ++q) {
+                    pos[size_t(q) * rep.stride32 + cell] = sp[q];
+                    pid[size_t(q) * rep.stride32 + cell] = si[q];
+                }
+            }
             att = uint32_t(rep.nt);
-            // written back in id order (the ids too, since the sort may have permuted them)
-            if (acc > 0 || n > 1) {
-#pragma unroll
-                for (int q = 0; q < CAP; ++q)
-                    if (q < n) pos[size_t(q) * rep.stride32 + cell] = P[q];
-            }
-            if (n > 1) {
-#pragma unroll
-                for (int q = 0; q < CAP; ++q)
-                    if (q < n) pid[size_t(q) * rep.stride32 + cell] = ids[q];
-            }
         }
         // no copy may still be landing in shared memory when the thread exits
         if constexpr (FIX) cp_async_wait_all();
@@ -367,11 +391,11 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
 template <bool FIX, int CAP, int NTC>
 static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                           unsigned long long* counters) {
-    const size_t smem = pass_smem(FIX, c.threads);
+    const size_t smem = pass_smem<FIX, CAP>(c.threads);
     static std::once_flag attr_once;
     std::call_once(attr_once, [&] {
         cudaFuncSetAttribute(k_pass<FIX, CAP, NTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(pass_smem(FIX, 256)));
+                             int(pass_smem<FIX, CAP>(256)));
     });
     return launch_k(k_pass<FIX, CAP, NTC>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R, table,
                     j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
