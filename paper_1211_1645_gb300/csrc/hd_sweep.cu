@@ -108,11 +108,28 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
     uint32_t di[2][kEagerSlots];
     P2<FIX> nq[2][kEagerSlots];
     int cxy[2][2];
+    // Fixed point: the shift difference has one sign per axis for the whole
+    // sweep, so a coordinate can only leave its cell on that side (the same
+    // integers as frame_change_fixed, with the impossible branch dropped).
+    auto step_fixed = [&](int32_t d, int c, int32_t u, int& c_out, int32_t& u_out) {
+        int32_t t = u + d;
+        if (d >= 0) {
+            if (t >= rep.W) {
+                t -= rep.W;
+                c = c + 1 == m ? 0 : c + 1;
+            }
+        } else if (t < 0) {
+            t += rep.W;
+            c = c == 0 ? m - 1 : c - 1;
+        }
+        c_out = c;
+        u_out = t;
+    };
     auto move = [&](const P2<FIX>& q, int cx, int cy, uint32_t& d, P2<FIX>& out) {
         int tcx, tcy;
         if constexpr (FIX) {
-            frame_change_fixed(sd.fx, rep.W, m, cx, q.x, tcx, out.x);
-            frame_change_fixed(sd.fy, rep.W, m, cy, q.y, tcy, out.y);
+            step_fixed(sd.fx, cx, q.x, tcx, out.x);
+            step_fixed(sd.fy, cy, q.y, tcy, out.y);
         } else {
             frame_change_fp64(sd.dx, rep.w, rep.w_below, m, cx, q.x, tcx, out.x);
             frame_change_fp64(sd.dy, rep.w, rep.w_below, m, cy, q.y, tcy, out.y);
@@ -149,6 +166,7 @@ k_rebuild(const Rep* __restrict__ reps, int R, const Frame* __restrict__ table, 
             }
         }
         // crowded old cells (rare): the remaining disks one at a time
+        if (n[h] > kEagerSlots)
         for (int k = kEagerSlots; k < n[h]; ++k) {
             uint32_t d;
             P2<FIX> q;
