@@ -102,3 +102,34 @@ def test_table1_mpmc_pressure_anchor(hd):
     print(f"P* = {means.mean():.5f} +- {se:.5f} (replica means {np.round(means, 4).tolist()}), paper {want} +- {want_se}")
     assert abs(means.mean() - want) < 3.0 * np.hypot(se, want_se)
     g.close()
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(__import__("os").environ.get("HD_SLOW") != "1",
+                    reason="a few minutes of GPU time: set HD_SLOW=1")
+def test_fixed_vs_fp64_equation_of_state_long(hd):
+    """The fixed-point chain's pressure at eta = 0.716 (N = 128^2) must agree
+    with the FP64 chain's within three combined standard errors: eight
+    independent replicas per form, 10^6 sweeps of equilibration from the
+    square lattice, then 10^6 sweeps with the contact pressure every 1000
+    sweeps.  The two forms are different Markov chains of the same ensemble,
+    so the comparison is statistical."""
+    import os
+    R, N, eta = 8, 128 * 128, 0.716
+    equil = int(os.environ.get("HD_SLOW_EQUIL", "1000000"))
+    prod = int(os.environ.get("HD_SLOW_PROD", "1000000"))
+    every = 1000
+    out = {}
+    for form, seed0 in (("fixed", 300), ("fp64", 400)):
+        g = hd.HardDisks([N] * R, [eta] * R, [0.1] * R, [seed0 + r for r in range(R)], precision=form)
+        g.run(equil // every, every, False)
+        g.series_reserve(prod // every + 8)
+        g.run(prod // every, every, True)
+        s = g.series()
+        etas = np.array([g.geometry(r)["eta"] for r in range(R)])
+        means = (s[:, :, 0] * 4.0 * etas / np.pi).mean(axis=0)  # P* per replica
+        out[form] = (means.mean(), means.std(ddof=1) / np.sqrt(R))
+        g.close()
+    (mf, sf), (md, sd) = out["fixed"], out["fp64"]
+    print(f"P* fixed {mf:.5f} +- {sf:.5f}, FP64 {md:.5f} +- {sd:.5f}, difference {(mf - md) / np.hypot(sf, sd):.2f} SE")
+    assert abs(mf - md) < 3.0 * np.hypot(sf, sd)
