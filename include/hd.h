@@ -59,7 +59,8 @@ typedef struct hd_opts {
     int32_t trials_per_cell; /* n_t, trial moves per occupied active cell and pass;
                                 Sec. II.B fixes it independent of occupancy
                                 [ceil(N / m^2), per replica]                        */
-    int32_t hist_bins;       /* K, contact-histogram bins [50]                      */
+    int32_t hist_bins;       /* K, contact-histogram bins, 5..512 (the quartic fit
+                                needs five) [50]                                    */
     double hist_dr;          /* bin width in sigma [1e-3]; Sec. II.C.1              */
     double cell_min;         /* minimum cell side in sigma, >= 2 [2]; Sec. II.B     */
     int32_t block_threads;   /* threads per block of the split sweep kernels [128]  */

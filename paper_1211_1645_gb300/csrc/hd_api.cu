@@ -76,6 +76,7 @@ struct hd_ctx {
     double* edges = nullptr;
     long long* edgesF = nullptr;
     double* fit = nullptr;
+    double* fit_qr = nullptr;  // Householder factor of the fit's design matrix
     double2* psi_local = nullptr;
     double2* psi_part = nullptr;
     double* psi_res = nullptr;
@@ -416,7 +417,7 @@ cudaError_t enqueue_pressure(hd_ctx* ctx, cudaStream_t s, bool capturing) {
     const hd::HistCfg h{ctx->K, ctx->edges, ctx->edgesF, halo};
     e = launch(ctx, HD_K_HIST, [&] { return hd::launch_hist(c, h, ctx->buf[ctx->cur], ctx->hist); }, capturing);
     if (e != cudaSuccess) return e;
-    return launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->hist, ctx->fit); }, capturing);
+    return launch(ctx, HD_K_FIT, [&] { return hd::launch_fit(c, ctx->K, ctx->fit_qr, ctx->hist, ctx->fit); }, capturing);
 }
 
 // Enqueue psi_6 (local field into psi_local when `local`) and its reduction.
@@ -492,7 +493,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     }
     if (o.precision != HD_FP64 && o.precision != HD_FIXED32) return HD_ERR_ARG;
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
-    if (!(o.cell_min >= 2.0) || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
+    if (!(o.cell_min >= 2.0) || o.hist_bins < 5 || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
     if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
     if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT && o.sweep_kernel != HD_SWEEP_TMA)
         return HD_ERR_ARG;
@@ -622,6 +623,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ok = ok && dev_alloc(ctx, &ctx->edges, size_t(ctx->K + 1));
     ok = ok && dev_alloc(ctx, &ctx->edgesF, size_t(ctx->K + 1));
     ok = ok && dev_alloc(ctx, &ctx->fit, size_t(4 * R));
+    ok = ok && dev_alloc(ctx, &ctx->fit_qr, hd::fit_factor_len(ctx->K));
     ok = ok && dev_alloc(ctx, &ctx->psi_local, size_t(ctx->Ntot));
     ok = ok && dev_alloc(ctx, &ctx->psi_part, size_t(ctx->blocks_t32));
     ok = ok && dev_alloc(ctx, &ctx->psi_res, size_t(2 * R));
@@ -647,6 +649,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     cu = cu && cudaMemset(ctx->err, 0, sizeof(int)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->buf[0].cnt, 0, size_t(ctx->Ctot) + kCellPad) == cudaSuccess;
     cu = cu && cudaMemset(ctx->buf[1].cnt, 0, size_t(ctx->Ctot) + kCellPad) == cudaSuccess;
+    cu = cu && hd::launch_fit_factor(nullptr, ctx->K, ctx->fit_qr) == cudaSuccess;
+    cu = cu && cudaStreamSynchronize(nullptr) == cudaSuccess;  // before any work on the context's own stream
     if (!cu) {
         free_ctx(ctx);
         return HD_ERR_CUDA;

@@ -82,7 +82,12 @@ struct HistCfg {
     int halo;                 // largest histogram reach (cells) over the replicas
 };
 cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, unsigned long long* hist);
-cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res);
+// The quartic fit's design matrix depends on K alone: launch_fit_factor
+// writes its Householder factor (fit_factor_len(K) doubles) once per context,
+// launch_fit applies it to each measurement.
+size_t fit_factor_len(int K);
+cudaError_t launch_fit_factor(cudaStream_t s, int K, double* qr);
+cudaError_t launch_fit(const LaunchCfg& c, int K, const double* qr, const unsigned long long* hist, double* res);
 cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err);
 cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res);
 // Append (beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6) of every replica to

@@ -218,8 +218,16 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
 // ---------------------------------------------------------------------------
 // g(r) normalisation (Eq. 2, p = N^2 / 2), least-squares quartic in
 // t = (r - 2 sigma) / (K dr) by Householder QR, value at contact, and the
-// contact-value pressure (Eq. 4).  One warp per replica: the K rows are
-// spread over the lanes and every column norm and dot product is a warp sum.
+// contact-value pressure (Eq. 4).  The design matrix depends on K alone, so
+// k_fit_factor triangularises it once per context and k_fit applies the
+// stored reflectors to each measurement's g(r): the same operations, in the
+// same order, as a factorisation of [A | b] at every measurement.  One warp
+// per replica: the K rows are spread over the lanes and every column norm
+// and dot product is a warp sum.
+// Factor layout: [0, 5K) the K x 5 matrix row-major after triangularisation
+// (R on and above the diagonal, reflector j's tail below it); [5K, 5K + 5)
+// v0_j, the first element of reflector j; [5K + 5, 5K + 10) v_j^T v_j, 0 for a
+// column with zero norm (no reflector).
 // res[4r + 0..3] = beta P / rho, g(2 sigma+), P* = beta P (2 sigma)^2, eta.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -228,10 +236,57 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K,
+__global__ void __launch_bounds__(32) k_fit_factor(int K, double* __restrict__ qr) {
+    __shared__ double A[kMaxFitBins * 5];
+    const int lane = threadIdx.x;
+    for (int k = lane; k < K; k += 32) {
+        const double t = __ddiv_rn(__dadd_rn(double(k), 0.5), double(K));
+        double tp = 1.0;
+        for (int q = 0; q < 5; ++q) {
+            A[k * 5 + q] = tp;
+            tp = __dmul_rn(tp, t);
+        }
+    }
+    __syncwarp();
+    for (int j = 0; j < 5; ++j) {
+        double part = 0.0;
+        for (int i = j + lane; i < K; i += 32) part = __dadd_rn(part, __dmul_rn(A[i * 5 + j], A[i * 5 + j]));
+        const double nrm2 = warp_sum(part);
+        const double nrm = sqrt(nrm2);
+        if (nrm == 0.0) {
+            if (lane == 0) {
+                qr[5 * K + j] = 0.0;
+                qr[5 * K + 5 + j] = 0.0;
+            }
+            continue;
+        }
+        const double ajj = A[j * 5 + j];
+        const double alpha = ajj > 0.0 ? -nrm : nrm;
+        const double v0 = __dsub_rn(ajj, alpha);
+        const double vtv = __dadd_rn(__dsub_rn(nrm2, __dmul_rn(ajj, ajj)), __dmul_rn(v0, v0));
+        __syncwarp();
+        if (lane == 0) A[j * 5 + j] = v0;  // v = (v0, A[j+1.., j])
+        __syncwarp();
+        for (int q = j + 1; q < 5; ++q) {
+            double dp = 0.0;
+            for (int i = j + lane; i < K; i += 32) dp = __dadd_rn(dp, __dmul_rn(A[i * 5 + j], A[i * 5 + q]));
+            const double sc = __ddiv_rn(__dmul_rn(2.0, warp_sum(dp)), vtv);
+            for (int i = j + lane; i < K; i += 32) A[i * 5 + q] = __dsub_rn(A[i * 5 + q], __dmul_rn(sc, A[i * 5 + j]));
+            __syncwarp();
+        }
+        if (lane == 0) {
+            A[j * 5 + j] = alpha;  // R diagonal
+            qr[5 * K + j] = v0;
+            qr[5 * K + 5 + j] = vtv;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < 5 * K; i += 32) qr[i] = A[i];
+}
+
+__global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K, const double* __restrict__ qr,
                                             const unsigned long long* __restrict__ hist, double* __restrict__ res) {
     pdl_begin();
-    __shared__ double A[kMaxFitBins * 5];
     __shared__ double b[kMaxFitBins];
     const int r = blockIdx.x, lane = threadIdx.x;
     const Rep& rep = reps[r];
@@ -243,48 +298,25 @@ __global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K,
         const double rk = __dadd_rn(2.0, __dmul_rn(__dadd_rn(double(k), 0.5), dr));
         const double shell = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, PI), rk), dr), V);
         b[k] = __ddiv_rn(__ddiv_rn(double(hist[size_t(r) * K + k]), p), shell);
-        const double t = __ddiv_rn(__dadd_rn(double(k), 0.5), double(K));
-        double tp = 1.0;
-        for (int q = 0; q < 5; ++q) {
-            A[k * 5 + q] = tp;
-            tp = __dmul_rn(tp, t);
-        }
     }
     __syncwarp();
-    // Householder triangularisation of the K x 5 design matrix, applied to b
+    // b <- Q^T b, reflector by reflector
     for (int j = 0; j < 5; ++j) {
-        double part = 0.0;
-        for (int i = j + lane; i < K; i += 32) part = __dadd_rn(part, __dmul_rn(A[i * 5 + j], A[i * 5 + j]));
-        const double nrm2 = warp_sum(part);
-        const double nrm = sqrt(nrm2);
-        if (nrm == 0.0) continue;
-        const double ajj = A[j * 5 + j];
-        const double alpha = ajj > 0.0 ? -nrm : nrm;
-        const double v0 = __dsub_rn(ajj, alpha);
-        const double vtv = __dadd_rn(__dsub_rn(nrm2, __dmul_rn(ajj, ajj)), __dmul_rn(v0, v0));
-        __syncwarp();
-        if (lane == 0) A[j * 5 + j] = v0;  // v = (v0, A[j+1.., j])
-        __syncwarp();
-        for (int q = j + 1; q <= 5; ++q) {  // q == 5 is the right-hand side b
-            double dp = 0.0;
-            for (int i = j + lane; i < K; i += 32)
-                dp = __dadd_rn(dp, __dmul_rn(A[i * 5 + j], q < 5 ? A[i * 5 + q] : b[i]));
-            const double sc = __ddiv_rn(__dmul_rn(2.0, warp_sum(dp)), vtv);
-            for (int i = j + lane; i < K; i += 32) {
-                if (q < 5) A[i * 5 + q] = __dsub_rn(A[i * 5 + q], __dmul_rn(sc, A[i * 5 + j]));
-                else b[i] = __dsub_rn(b[i], __dmul_rn(sc, A[i * 5 + j]));
-            }
-            __syncwarp();
-        }
-        if (lane == 0) A[j * 5 + j] = alpha;  // R diagonal
+        const double vtv = qr[5 * K + 5 + j];
+        if (vtv == 0.0) continue;
+        const double v0 = qr[5 * K + j];
+        double dp = 0.0;
+        for (int i = j + lane; i < K; i += 32) dp = __dadd_rn(dp, __dmul_rn(i == j ? v0 : qr[i * 5 + j], b[i]));
+        const double sc = __ddiv_rn(__dmul_rn(2.0, warp_sum(dp)), vtv);
+        for (int i = j + lane; i < K; i += 32) b[i] = __dsub_rn(b[i], __dmul_rn(sc, i == j ? v0 : qr[i * 5 + j]));
         __syncwarp();
     }
     if (lane != 0) return;
     double coef[5];
     for (int j = 4; j >= 0; --j) {
         double acc = b[j];
-        for (int q = j + 1; q < 5; ++q) acc = __dsub_rn(acc, __dmul_rn(A[j * 5 + q], coef[q]));
-        coef[j] = __ddiv_rn(acc, A[j * 5 + j]);
+        for (int q = j + 1; q < 5; ++q) acc = __dsub_rn(acc, __dmul_rn(qr[j * 5 + q], coef[q]));
+        coef[j] = __ddiv_rn(acc, qr[j * 5 + j]);
     }
     const double g0 = coef[0];
     const double eta = __ddiv_rn(__dmul_rn(double(rep.N), PI), V);
@@ -616,9 +648,17 @@ cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, un
     return c.cap == 4 ? hist_t<false, 4>(c, h, cells, hist) : hist_t<false, 9>(c, h, cells, hist);
 }
 
-cudaError_t launch_fit(const LaunchCfg& c, int K, const unsigned long long* hist, double* res) {
-    if (K > kMaxFitBins) return cudaErrorInvalidValue;
-    return launch_k(k_fit, dim3(c.R), dim3(32), 0, c.stream, c.reps, K, hist, res);
+size_t fit_factor_len(int K) { return size_t(5 * K + 10); }
+
+cudaError_t launch_fit_factor(cudaStream_t s, int K, double* qr) {
+    if (K < 5 || K > kMaxFitBins) return cudaErrorInvalidValue;
+    k_fit_factor<<<1, 32, 0, s>>>(K, qr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const LaunchCfg& c, int K, const double* qr, const unsigned long long* hist, double* res) {
+    if (K < 5 || K > kMaxFitBins) return cudaErrorInvalidValue;
+    return launch_k(k_fit, dim3(c.R), dim3(32), 0, c.stream, c.reps, K, qr, hist, res);
 }
 
 template <bool FIX, int CAP>

@@ -25,14 +25,15 @@ namespace hd {
 __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__ table,
                         Frame* __restrict__ cur, uint64_t* __restrict__ sweep_ctr, int nchunk) {
     pdl_begin();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    const Rep rep = reps[r];
+    // one block per replica, one thread per sweep of the chunk: every sweep's
+    // draws come from its own generator block
+    const int r = blockIdx.x;
+    const Rep& rep = reps[r];
     Frame* t = table + size_t(r) * (kMaxChunk + 1);
-    t[0] = cur[r];
     const uint64_t s0 = sweep_ctr[r];
-    Frame f;
-    for (int j = 1; j <= nchunk; ++j) {
+    if (threadIdx.x == 0) t[0] = cur[r];
+    for (int j = 1 + int(threadIdx.x); j <= nchunk; j += int(blockDim.x)) {
+        Frame f;
         const uint32_t s = uint32_t(s0 + uint64_t(j - 1));
         const uint4 a = philox(s, 0u, 0u, kTagSweep, rep.key0, rep.key1);
         f.sx = __dmul_rn(double(a.x) * 0x1p-32, rep.w);
@@ -58,8 +59,13 @@ __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__
         f.perm = perm;
         t[j] = f;
     }
-    cur[r] = t[nchunk];
-    sweep_ctr[r] = s0 + uint64_t(nchunk);
+    // every thread has read sweep_ctr[r], thread 0 has read cur[r], and the
+    // chunk's last frame is visible to the block
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cur[r] = t[nchunk];
+        sweep_ctr[r] = s0 + uint64_t(nchunk);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -392,7 +398,7 @@ k_positions(const Rep* __restrict__ reps, int R, const Frame* __restrict__ cur, 
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t* sweep_ctr, int nchunk) {
-    return launch_k(k_draws, dim3((c.R + 63) / 64), dim3(64), 0, c.stream, c.reps, c.R, table, cur, sweep_ctr, nchunk);
+    return launch_k(k_draws, dim3(c.R), dim3(128), 0, c.stream, c.reps, c.R, table, cur, sweep_ctr, nchunk);
 }
 
 template <bool FIX, int CAP>

@@ -59,6 +59,7 @@ def test_status_strings_and_defaults(hdlib):
     (9, 0.7, 1.0, 0.1, {}),                       # fewer than 4 cells per side
     (256, 0.7, 1.0, 0.1, {"cell_min": 1.5}),      # cells narrower than a diameter
     (256, 0.7, 1.0, 0.1, {"hist_bins": 10000}),   # too many bins for the fit
+    (256, 0.7, 1.0, 0.1, {"hist_bins": 4}),       # too few bins for a quartic
     (256, 0.7, 1.0, 0.1, {"block_threads": 100}),  # not a warp multiple
 ])
 def test_invalid_arguments_rejected_on_host(hdlib, N, eta, sigma, delta, kw):
