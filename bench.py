@@ -13,10 +13,13 @@ step, outside the events.  Under torchrun each rank runs its own replica
 (seed + rank, weak scaling) and rank 0 reports the max time over ranks.
 Each step is one graph launch of the library (hd_run).
 
-Secondary keys of the same line (same step and timing): `fp64` (the plain
-FP64 chain), `replicas4` (four replicas of the headline system in one
-context), `scan31` (the 31-replica equation-of-state scan) and `autotuned`
-(the headline system at the cell side and block size the autotuner picks).
+Secondary keys of the same line (same step and timing): `sweeps_only` (the
+same S sweeps without the measurement), `fp64` (the plain FP64 chain),
+`replicas4` (four replicas of the headline system in one context), `scan31`
+(the 31-replica equation-of-state scan) and `autotuned` (the headline system
+at the cell side and block size the autotuner picks).  `roofline.ncu` holds
+the committed ncu figures (L2 and pipe utilisation, issue activity,
+occupancy) of the dominant kernel while its sources are unchanged.
 
 --impl reference times the CPU oracle (one core) on a bounded sample of the
 same workload instead.
@@ -157,7 +160,7 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # the GPU arm
 # ---------------------------------------------------------------------------
 def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
-              block_threads=128, sweep_kernel=None):
+              block_threads=128, sweep_kernel=None, measure=True):
     """Device-resident timing of `steps` steps of one form; returns a dict.
     N and eta may be per-replica lists (one batched context); attempts are
     summed over replicas."""
@@ -185,10 +188,11 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     S = args.sweeps_per_step
 
     # one step = one graph launch: S sweeps + pressure and Psi_6 recorded on the device
+    # (measure=False: the S sweeps alone)
     sysg.series_reserve(warmup + steps + 8)
 
     def step():
-        sysg.run(1, S, True)
+        sysg.run(1, S, measure)
 
     for _ in range(warmup):
         step()
@@ -373,6 +377,21 @@ def kernel_sources_hash(kernel=None):
     return h.hexdigest()[:16]
 
 
+def recorded_counters(kernel):
+    """Other ncu figures of one launch of `kernel` (L2 and pipe utilisation,
+    issue activity, occupancy) from the committed summaries, or None when no
+    summary was taken on the current kernel sources."""
+    import glob
+    import re
+    want = kernel_sources_hash(kernel)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            mt = re.match(r"\s*counters (\S+) (.*) sources=(\w+)\s*$", line)
+            if mt and mt.group(1) == f"k_{kernel}" and mt.group(3) == want:
+                return {k: float(v) for k, v in (kv.split("=") for kv in mt.group(2).split())}
+    return None
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summaries,
     or None when no summary was taken on the current kernel sources."""
@@ -405,6 +424,11 @@ def run_ours(args):
         t64, a64 = reduce_max_sum(world, r["ms"], float(r["attempts"]), dev)
         fp64 = {"value": a64 / (t64 / 1e3), "ms_per_step": t64 / max(1, args.steps // 2),
                 "kernel_ms_per_step": {k: v[0] / 2 for k, v in r["kernel_times"].items() if v[1]}}
+    # the sweep loop alone (rebuild + four colour passes per sweep), same timing
+    so = time_form(args, args.form, rank, world, max(1, args.steps // 2), 2, measure=False)
+    tso, aso = reduce_max_sum(world, so["ms"], float(so["attempts"]), dev)
+    sweeps_only = {"value": aso / (tso / 1e3), "unit": UNIT, "ms_per_step": tso / max(1, args.steps // 2),
+                   "config": f"{args.sweeps_per_step} sweeps per step, no measurement"}
     e2e = None
     if not args.no_e2e:
         e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2))
@@ -441,12 +465,14 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top),
                      "kernel": top, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg, "avg_launch_us": top_avg_s * 1e6},
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_us": top_avg_s * 1e6,
+                     "ncu": recorded_counters(top)},
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
         "kernel_ms_per_step": {k: v[0] / 2 for k, v in kt.items() if v[1]},
         "last_measurement": dict(zip(["betaP_over_rho", "g_contact", "psi6_re", "psi6_im"],
                                      main["last_measurement"] or [])),
+        "sweeps_only": sweeps_only,
         "fp64": fp64,
         "e2e": e2e,
     }

@@ -83,3 +83,31 @@ def test_algorithmic_bytes():
     assert bench.algorithmic_bytes("sweep", N, m, "fixed") == 2 * (N * 12 + m * m)
     assert bench.algorithmic_bytes("pass", N, m, "fixed") == m * m + N * 8 + (N // 4) * 8
     assert bench.algorithmic_bytes("pass", N, m, "fp64") == m * m + N * 16 + (N // 4) * 16
+
+
+def test_recorded_profile_figures_follow_kernel_sources(tmp_path, monkeypatch):
+    """Traffic and counter lines of a profile summary are used only while the
+    kernel's sources hash to the value recorded beside them."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_1211_1645_gb300", "csrc")
+    dst = tmp_path / "paper_1211_1645_gb300" / "csrc"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("*.o", "*.so"))
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_sources_hash("pass")
+    (tmp_path / "profiles" / "k.md").write_text(
+        "text\n"
+        f"    traffic k_pass bytes_per_launch=123 sources={h}\n"
+        f"    counters k_pass l2_pct=14.5 issue_active_pct=45.25 sources={h}\n"
+        "    traffic k_rebuild bytes_per_launch=456 sources=0000000000000000\n")
+    assert bench.recorded_traffic("pass") == 123
+    assert bench.recorded_counters("pass") == {"l2_pct": 14.5, "issue_active_pct": 45.25}
+    assert bench.recorded_traffic("rebuild") is None
+    assert bench.recorded_counters("rebuild") is None
+    # a changed source invalidates the recorded figures
+    with open(dst / "hd_sweep.cu", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.recorded_traffic("pass") is None
+    assert bench.recorded_counters("pass") is None
