@@ -377,33 +377,32 @@ def kernel_sources_hash(kernel=None):
     return h.hexdigest()[:16]
 
 
-def recorded_counters(kernel):
-    """Other ncu figures of one launch of `kernel` (L2 and pipe utilisation,
-    issue activity, occupancy) from the committed summaries, or None when no
-    summary was taken on the current kernel sources."""
+def _recorded(kind, kernel, workload):
+    """Key=value figures of a `kind` line ("traffic" or "counters") for
+    `kernel` on `workload` ("<N>_<form>") in the committed ncu summaries,
+    taken on the current kernel sources; None when there is none."""
     import glob
     import re
     want = kernel_sources_hash(kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
-            mt = re.match(r"\s*counters (\S+) (.*) sources=(\w+)\s*$", line)
-            if mt and mt.group(1) == f"k_{kernel}" and mt.group(3) == want:
+            mt = re.match(rf"\s*{kind} (\S+) (.*) workload=(\S+) sources=(\w+)\s*$", line)
+            if mt and mt.group(1) == f"k_{kernel}" and mt.group(3) == workload and mt.group(4) == want:
                 return {k: float(v) for k, v in (kv.split("=") for kv in mt.group(2).split())}
     return None
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summaries,
-    or None when no summary was taken on the current kernel sources."""
-    import glob
-    import re
-    want = kernel_sources_hash(kernel)
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        for line in open(path):
-            mt = re.match(r"\s*traffic (\S+) bytes_per_launch=(\d+) sources=(\w+)", line)
-            if mt and mt.group(1) == f"k_{kernel}" and mt.group(3) == want:
-                return int(mt.group(2))
-    return None
+def recorded_counters(kernel, workload):
+    """Other ncu figures of one launch of `kernel` (L2 and pipe utilisation,
+    issue activity, occupancy) from the committed summaries, or None."""
+    return _recorded("counters", kernel, workload)
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summaries, or None."""
+    d = _recorded("traffic", kernel, workload)
+    return int(d["bytes_per_launch"]) if d else None
 
 
 def run_ours(args):
@@ -463,10 +462,10 @@ def run_ours(args):
                    "acceptance": main["acceptance"], "l2": "flushed before each timed step (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top),
+                     "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top, f"{args.N}_{args.form}"),
                      "kernel": top, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg, "avg_launch_us": top_avg_s * 1e6,
-                     "ncu": recorded_counters(top)},
+                     "ncu": recorded_counters(top, f"{args.N}_{args.form}")},
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
         "kernel_ms_per_step": {k: v[0] / 2 for k, v in kt.items() if v[1]},

@@ -99,15 +99,19 @@ def test_recorded_profile_figures_follow_kernel_sources(tmp_path, monkeypatch):
     h = bench.kernel_sources_hash("pass")
     (tmp_path / "profiles" / "k.md").write_text(
         "text\n"
-        f"    traffic k_pass bytes_per_launch=123 sources={h}\n"
-        f"    counters k_pass l2_pct=14.5 issue_active_pct=45.25 sources={h}\n"
-        "    traffic k_rebuild bytes_per_launch=456 sources=0000000000000000\n")
-    assert bench.recorded_traffic("pass") == 123
-    assert bench.recorded_counters("pass") == {"l2_pct": 14.5, "issue_active_pct": 45.25}
-    assert bench.recorded_traffic("rebuild") is None
-    assert bench.recorded_counters("rebuild") is None
+        f"    traffic k_pass bytes_per_launch=999 workload=4194304_fixed sources={h}\n"
+        f"    traffic k_pass bytes_per_launch=123 workload=1048576_fixed sources={h}\n"
+        f"    counters k_pass l2_pct=14.5 issue_active_pct=45.25 workload=1048576_fixed sources={h}\n"
+        "    traffic k_rebuild bytes_per_launch=456 workload=1048576_fixed sources=0000000000000000\n")
+    w = "1048576_fixed"
+    assert bench.recorded_traffic("pass", w) == 123
+    assert bench.recorded_traffic("pass", "4194304_fixed") == 999
+    assert bench.recorded_traffic("pass", "1048576_fp64") is None
+    assert bench.recorded_counters("pass", w) == {"l2_pct": 14.5, "issue_active_pct": 45.25}
+    assert bench.recorded_traffic("rebuild", w) is None
+    assert bench.recorded_counters("rebuild", w) is None
     # a changed source invalidates the recorded figures
     with open(dst / "hd_sweep.cu", "a") as f:
         f.write("\n// changed\n")
-    assert bench.recorded_traffic("pass") is None
-    assert bench.recorded_counters("pass") is None
+    assert bench.recorded_traffic("pass", w) is None
+    assert bench.recorded_counters("pass", w) is None
