@@ -133,3 +133,51 @@ def test_fixed_vs_fp64_equation_of_state_long(hd):
     (mf, sf), (md, sd) = out["fixed"], out["fp64"]
     print(f"P* fixed {mf:.5f} +- {sf:.5f}, FP64 {md:.5f} +- {sd:.5f}, difference {(mf - md) / np.hypot(sf, sd):.2f} SE")
     assert abs(mf - md) < 3.0 * np.hypot(sf, sd)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(__import__("os").environ.get("HD_SLOW") != "1",
+                    reason="about ten minutes of GPU time: set HD_SLOW=1")
+def test_table2_psi6_correlation_time(hd):
+    """Table II: at N = 512^2, eta = 0.698 the Psi_6 correlation time of MPMC
+    is 8e5 displacements per disk.  Four fixed-point replicas from the square
+    lattice, delta tuned to 30% acceptance (the paper leaves MPMC's step to
+    'optimal internal parameters'), 2e6 sweeps of equilibration, then 1e7
+    sweeps with Psi_6 recorded every 1000.  tau comes from the Eq. 9
+    autocorrelation, averaged over the replicas, fitted (ln Re C against the
+    lag) where 0.05 < Re C < 0.5, and is converted to displacements per disk
+    with the chain's attempts per disk per sweep.  The step size enters tau,
+    so the check is loose: within a factor of four of the paper's value."""
+    import os
+    import time as _time
+    R, N, eta = 4, 512 * 512, 0.698
+    equil = int(os.environ.get("HD_SLOW_EQUIL", "2000000"))
+    prod = int(os.environ.get("HD_SLOW_PROD", "10000000"))
+    every = 1000
+    g = hd.HardDisks([N] * R, [eta] * R, [0.1] * R, [501 + r for r in range(R)], precision="fixed")
+    g.run(200, 100, False)
+    delta = g.tune_delta(0.3, 50, 20)
+    g.run(equil // every, every, False)
+    a0, c0 = (x.sum() for x in g.stats())
+    g.series_reserve(prod // every + 8)
+    t0 = _time.perf_counter()
+    g.run(prod // every, every, True)
+    a1, c1 = (x.sum() for x in g.stats())  # synchronises
+    wall = _time.perf_counter() - t0
+    disp_per_sweep = float(a1 - a0) / (R * N * (prod // every) * every)  # attempts per disk per sweep
+    T = prod // every
+    C = g.psi6_acf(T // 3).real.mean(axis=0)
+    lags = np.arange(C.size)
+    sel = (C > 0.05) & (C < 0.5)
+    assert sel.sum() >= 5, f"no exponential window: C = {np.round(C[:50], 3).tolist()}"
+    slope = np.polyfit(lags[sel], np.log(C[sel]), 1)[0]
+    tau_steps = -1.0 / slope
+    tau_lib = g.psi6_tau(int(lags[sel][0]), int(lags[sel][-1]))
+    tau_disp = tau_steps * every * disp_per_sweep
+    s_per_tau = wall / (prod / every) * tau_steps
+    print(f"delta {np.round(delta, 4).tolist()}, acceptance {float(c1 - c0) / float(a1 - a0):.3f}, "
+          f"tau = {tau_steps:.0f} recorded steps = {tau_disp:.3g} displacements per disk "
+          f"(per replica {np.round(tau_lib * every * disp_per_sweep, -3).tolist()}), paper 8e5; "
+          f"{s_per_tau:.1f} s of GPU time per tau for the four replicas")
+    assert 8e5 / 4 < tau_disp < 8e5 * 4
+    g.close()
