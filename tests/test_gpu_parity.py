@@ -195,6 +195,29 @@ def test_full_size_N1048576_coexistence(hd, oracle_mod, form, kernel):
     assert abs(glob[0] - rglob) <= 1e-12
 
 
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_full_size_bench_step(hd, oracle_mod, form):
+    """The benchmark's own launch path at its size: N = 1024^2, eta = 0.716,
+    seed 1, one graph-captured step of 100 sweeps and a device-side
+    measurement on a library stream of the caller's (hd_run, as bench.py
+    times it); series entry, trial counts and every position against the
+    oracle after the same 100 sweeps."""
+    import torch
+    N = 1024 * 1024
+    g, o = make_pair(hd, oracle_mod, form, N, 0.716, 0.1, 1)
+    s = torch.cuda.Stream()
+    g.set_stream(s.cuda_stream)
+    g.series_reserve(4)
+    g.run(1, 100, measure=True)
+    ser = g.series()
+    o.sweep(100)
+    want = oracle_mod.contact_pressure(o.histogram(50, 1e-3), N, o.geometry()["L"], o.realised_dr(1e-3))
+    _, rglob = o.psi6()
+    assert abs(ser[0, 0, 0] - want["betaP_over_rho"]) <= 1e-12 * want["betaP_over_rho"]
+    assert abs(complex(ser[0, 0, 2], ser[0, 0, 3]) - rglob) <= 1e-12
+    assert_same_state(g, o)
+
+
 def test_full_size_N4194304_shifted_rows(hd, oracle_mod):
     """N = 2048^2 at eta = 0.720 from the shifted-row lattice, fixed point."""
     N = 2048 * 2048
