@@ -229,6 +229,39 @@ def test_full_size_N4194304_shifted_rows(hd, oracle_mod):
     assert np.array_equal(hist[0], o.histogram(50, 1e-3))
 
 
+def test_largest_size_N16777216(hd, oracle_mod):
+    """N = 4096^2 at eta = 0.716, fixed point: the largest N of the
+    allocation-free Psi_6 mean (4096 blocks of 4096 values) and 16x the
+    benchmark.  Whole state, histogram and every psi_j after one sweep, and
+    the allocation-free mean of the library's own psi_j field at exactly its
+    size limit."""
+    import ctypes
+    import torch
+    N = 4096 * 4096
+    g, o = make_pair(hd, oracle_mod, "fixed", N, 0.716, 0.1, 11)
+    g.sweep(1)
+    o.sweep(1)
+    assert_same_state(g, o)
+    _, _, hist = g.pressure()
+    assert np.array_equal(hist[0], o.histogram(50, 1e-3))
+    glob, loc = g.psi6()
+    rloc, rglob = o.psi6()
+    assert np.abs(loc - rloc).max() <= PSI_TOL["fixed"]
+    assert abs(glob[0] - rglob) <= 1e-12
+    del o, rloc
+    field = torch.from_numpy(np.stack([loc.real, loc.imag], 1).copy()).to("cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    lib = hd.load()
+    st = lib.hd_psi6_mean_noalloc(ctypes.c_void_p(field.data_ptr()), ctypes.c_int64(N),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(0))
+    torch.cuda.synchronize()
+    assert st == 0
+    got = out.cpu().numpy()
+    assert abs(complex(got[0], got[1]) - glob[0]) <= 1e-12
+    g.close()
+
+
 def test_reach_error_is_reported_and_recoverable(hd, oracle_mod):
     from paper_1211_1645_gb300.hd import HD_ERR_REACH, HDError
     g = hd.HardDisks(2, 2 * math.pi / 100, 1.0, 4, hist_bins=500, hist_dr=0.01)
