@@ -154,6 +154,25 @@ bool dev_alloc(hd_ctx* ctx, T** p, size_t count) {
     return true;
 }
 
+// Bounds of the FP64 form's float pre-test of a pair (pair_clear).  With
+// t = 2^-20 (the relative error of approx_f32) and u = 2^-24 (float
+// rounding), and |q| < w, |cell offset| <= w, |np| < w + delta,
+// |rx| <= R = 2w + delta: the float difference errs by at most
+// E = t (2w + delta) + u (3w + R), the float square sum by
+// 4 R E + 2 E^2 + 4 u (R + E)^2, and the FP64 square sum by less than
+// 16 2^-53 R^2.  Twice their sum, M, brackets (2 sigma)^2 = 4: a float
+// estimate at or above 4 + M (below 4 - M) certifies a clear pair (an
+// overlap) exactly as the FP64 test would.
+void set_f32_bounds(Rep& r) {
+    const double t = std::ldexp(1.0, -20), u = std::ldexp(1.0, -24);
+    const double w = r.w, d = r.delta, R = 2.0 * w + d;
+    const double E = t * (2.0 * w + d) + u * (3.0 * w + R);
+    const double M = 2.0 * (4.0 * R * E + 2.0 * E * E + 4.0 * u * (R + E) * (R + E) + 16.0 * std::ldexp(1.0, -53) * R * R);
+    r.wf = float(w);
+    r.d2_lo = std::nextafter(float(4.0 - M), -HUGE_VALF);
+    r.d2_hi = std::nextafter(float(4.0 + M), HUGE_VALF);
+}
+
 // Geometry of one chain (Sec. II.A, II.B).  Lengths in units of sigma.
 hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64_t seed, const hd_opts& o,
                        Plan& pl) {
@@ -205,6 +224,7 @@ hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64
     r.sigma = sigma;
     r.key0 = uint32_t(seed & 0xffffffffu);
     r.key1 = uint32_t(seed >> 32);
+    set_f32_bounds(r);
     pl.nlat = n;
     pl.eta_req = eta;
     return HD_OK;
@@ -1009,6 +1029,7 @@ bool set_rep_delta(hd_ctx* ctx, int r, double delta) {
     } else {
         if (!(delta < rep.w)) return false;
         rep.delta = delta;
+        set_f32_bounds(rep);
     }
     return true;
 }

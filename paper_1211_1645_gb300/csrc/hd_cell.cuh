@@ -178,6 +178,19 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
         static_assert(kFxDiam2 == (int64_t(1) << 50), "the high-word test assumes (2 sigma)^2 = 2^50");
         return uint32_t(d2 >> 32) >= (1u << 18);
     } else {
+        // GB300's FP64 pipe is narrow, so the pair is first decided in float:
+        // when the float estimate of d^2 lies outside [d2_lo, d2_hi), which
+        // brackets 4 by the estimate's error bound (see plan_replica), it is
+        // on the same side of 4 as the FP64 value below.  Only pairs within
+        // that band of contact run the FP64 test.
+        const float npx = approx_f32(np.x), npy = approx_f32(np.y);
+        const float fx = approx_f32(q.x), fy = approx_f32(q.y);
+        const float ax = ox == 0 ? fx : __fadd_rn(fx, ox < 0 ? -rep.wf : rep.wf);
+        const float ay = oy == 0 ? fy : __fadd_rn(fy, oy < 0 ? -rep.wf : rep.wf);
+        const float sx = __fsub_rn(ax, npx), sy = __fsub_rn(ay, npy);
+        const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
+        if (d2f >= rep.d2_hi) return true;
+        if (d2f < rep.d2_lo) return false;
         // (q + 0) is q itself for the non-negative cell offsets, so a zero
         // cell difference skips that addition (an FP64 operation saved)
         const double qx = ox == 0 ? q.x : __dadd_rn(q.x, ox < 0 ? -rep.w : rep.w);

@@ -51,6 +51,11 @@ struct Rep {
     double sigma;       // disk radius (output scale)
     double dr;          // realised histogram bin width (sigma units)
     uint32_t key0, key1;
+    // FP64 form's float pre-test of a pair (see pair_clear): the cell side
+    // in float, and floats bracketing (2 sigma)^2 = 4 by the error bound of
+    // the float estimate of d^2
+    float wf, d2_lo, d2_hi;
+    int32_t pad_f;
 };
 
 // Draws of one sweep: the shift of its cell frame and its colour order.
@@ -88,6 +93,17 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// A float within a relative 2^-20 of x (|x| < 2^128), from the high word of
+// x alone (integer operations only, no FP64 instruction): the exponent
+// rebiased from 1023 to 127 and the 20 mantissa bits of the high word widened
+// to the float's 23 (truncation toward zero); |x| < 2^-126 gives 0.
+__device__ __forceinline__ float approx_f32(double x) {
+    const uint32_t hi = uint32_t(__double2hiint(x));
+    const uint32_t mag = hi & 0x7FFFFFFFu;
+    const uint32_t f = mag < (897u << 20) ? 0u : ((mag - (896u << 20)) << 3);
+    return __uint_as_float(f | (hi & 0x80000000u));
 }
 
 // floor(word * n / 2^32): an integer in [0, n).
