@@ -173,6 +173,27 @@ void set_f32_bounds(Rep& r) {
     r.d2_hi = std::nextafter(float(4.0 + M), HUGE_VALF);
 }
 
+// The same bound for the FP64 contact histogram's float pre-test
+// (k_hist_tile): a pair H = hist_R cells apart at most, so |rx| <= R =
+// (H + 1) w, with the float offset dcx wf (rounded product) added to the
+// neighbour's coordinate.  The float difference errs by at most
+// E = 2 t w + u w (4H + 2); a pair whose float estimate of r^2 lies outside
+// [edge_0 - M, edge_K + M) is outside the histogram's range in FP64.
+double cells_f32_margin(double w, int H) {
+    const double t = std::ldexp(1.0, -20), u = std::ldexp(1.0, -24);
+    const double R = (double(H) + 1.0) * w;
+    const double E = 2.0 * t * w + u * w * (4.0 * double(H) + 2.0);
+    return 2.0 * (4.0 * R * E + 2.0 * E * E + 4.0 * u * (R + E) * (R + E) + 16.0 * std::ldexp(1.0, -53) * R * R);
+}
+
+// The histogram bounds, and the psi_6 margin (candidates two cells apart).
+void set_hist_f32_bounds(Rep& r, double e0, double eK) {
+    const double M = cells_f32_margin(r.w, r.hist_R);
+    r.h_lo = std::nextafter(float(e0 - M), -HUGE_VALF);
+    r.h_hi = std::nextafter(float(eK + M), HUGE_VALF);
+    r.psi_m = std::nextafter(float(cells_f32_margin(r.w, 2)), HUGE_VALF);
+}
+
 // Geometry of one chain (Sec. II.A, II.B).  Lengths in units of sigma.
 hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64_t seed, const hd_opts& o,
                        Plan& pl) {
@@ -592,6 +613,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         } else {
             rep.dr = o.hist_dr;
             rep.hist_R = int(std::floor((2.0 + double(ctx->K) * o.hist_dr) / rep.w)) + 1;
+            const double xK = 2.0 + double(ctx->K) * o.hist_dr;  // as the squared bin edges below
+            set_hist_f32_bounds(rep, 4.0, xK * xK);
         }
         ctx->reps.push_back(rep);
         ctx->nlat.push_back(plans[size_t(r)].nlat);

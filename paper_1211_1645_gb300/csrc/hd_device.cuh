@@ -51,11 +51,11 @@ struct Rep {
     double sigma;       // disk radius (output scale)
     double dr;          // realised histogram bin width (sigma units)
     uint32_t key0, key1;
-    // FP64 form's float pre-test of a pair (see pair_clear): the cell side
-    // in float, and floats bracketing (2 sigma)^2 = 4 by the error bound of
-    // the float estimate of d^2
-    float wf, d2_lo, d2_hi;
-    int32_t pad_f;
+    // FP64 form's float pre-tests (see pair_clear, k_hist_tile, k_psi6): the
+    // cell side in float; floats bracketing (2 sigma)^2 = 4, and the
+    // histogram's squared range [edge_0, edge_K), by the error bounds of the
+    // float estimates of d^2; that bound for pairs two cells apart (psi_6)
+    float wf, d2_lo, d2_hi, h_lo, h_hi, psi_m;
 };
 
 // Draws of one sweep: the shift of its cell frame and its colour order.

@@ -180,6 +180,11 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
         const int own = int(s_list[d] >> 4), k = int(s_list[d] & 15u);
         const P2<FIX> me = s_pos[k * nS + own];
         const int32_t idme = s_id[k * nS + own];
+        float mfx = 0.0f, mfy = 0.0f;  // FP64 form: float images of the disk's offsets
+        if constexpr (!FIX) {
+            mfx = approx_f32(me.x);
+            mfy = approx_f32(me.y);
+        }
         for (int dcy = -RR; dcy <= RR; ++dcy) {
             for (int dcx = -RR; dcx <= RR; ++dcx) {
                 const int sc = own + dcy * SX + dcx;
@@ -195,6 +200,13 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
                         const int32_t ry = (o.y + dcy * rep.W) - me.y;
                         r2 = int64_t(rx) * rx + int64_t(ry) * ry;
                     } else {
+                        // float pre-test (as pair_clear's): a pair whose float
+                        // estimate of r^2 lies outside the range widened by its
+                        // error bound is outside it in FP64 too
+                        const float sx = __fsub_rn(__fadd_rn(approx_f32(o.x), __fmul_rn(float(dcx), rep.wf)), mfx);
+                        const float sy = __fsub_rn(__fadd_rn(approx_f32(o.y), __fmul_rn(float(dcy), rep.wf)), mfy);
+                        const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
+                        if (d2f < rep.h_lo || d2f >= rep.h_hi) continue;
                         const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
                         const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
                         r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
@@ -480,6 +492,11 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
             const int cx = X0 + (own - sy * kPsiSX) - kPsiHalo, cy = Y0 + sy - kPsiHalo;
             const P2<FIX> me = s_pos[k * nS + own];
             const int32_t idme = s_id[k * nS + own];
+            float mfx = 0.0f, mfy = 0.0f;  // FP64 form: float images of the disk's offsets
+            if constexpr (!FIX) {
+                mfx = approx_f32(me.x);
+                mfy = approx_f32(me.y);
+            }
             Nbr<FIX> nb;
             nb.n = 0;
             bool ok = false;
@@ -501,6 +518,18 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                                     const int32_t ry = (o.y + dcy * rep.W) - me.y;
                                     nb.insert(int64_t(rx) * rx + int64_t(ry) * ry, idq, rx, ry);
                                 } else {
+                                    if (nb.n == 6) {
+                                        // float pre-test: a candidate whose float estimate
+                                        // of r^2 exceeds the sixth key by more than the
+                                        // estimate's error bound is farther in FP64 too
+                                        // (approx_f32 truncates; the product rounds up
+                                        // past the key itself)
+                                        const float sx = __fsub_rn(__fadd_rn(approx_f32(o.x), __fmul_rn(float(dcx), rep.wf)), mfx);
+                                        const float sy = __fsub_rn(__fadd_rn(approx_f32(o.y), __fmul_rn(float(dcy), rep.wf)), mfy);
+                                        const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
+                                        const float k5 = __fmul_ru(approx_f32(nb.key[5]), 1.0f + 0x1p-19f);
+                                        if (d2f > __fadd_ru(k5, rep.psi_m)) continue;
+                                    }
                                     const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
                                     const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
                                     nb.insert(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), idq, rx, ry);

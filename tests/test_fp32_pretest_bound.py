@@ -72,3 +72,36 @@ def test_float_estimate_within_half_margin(w, d):
 def test_margin_is_small_at_the_benchmark_geometry():
     # the band that falls back to FP64 stays a tiny slice of the contact shell
     assert margin(2.0008917450904846, 0.1) < 5e-4
+
+
+def hist_margin(w, H):
+    t, u = 2.0 ** -20, 2.0 ** -24
+    R = (H + 1) * w
+    E = 2 * t * w + u * w * (4 * H + 2)
+    return 2 * (4 * R * E + 2 * E * E + 4 * u * (R + E) ** 2 + 16 * 2.0 ** -53 * R * R)
+
+
+@pytest.mark.parametrize("w,H", [(2.0008917450904846, 2), (2.0122, 2), (1.0 + 2.0 ** -10, 4), (7.9, 1)])
+def test_histogram_float_estimate_within_half_margin(w, H):
+    """k_hist_tile's FP64 pre-test: both coordinates in [0, w), the
+    neighbour H cells away at most, the offset dcx w added in float as
+    dcx * wf and in FP64 as a rounded product."""
+    rng = np.random.default_rng(2)
+    n = 400000
+    M = hist_margin(w, H)
+    wf = np.float32(w)
+    ox = rng.integers(-H, H + 1, n)
+    oy = rng.integers(-H, H + 1, n)
+    qx, qy = rng.uniform(0, w, n), rng.uniform(0, w, n)
+    mx, my = rng.uniform(0, w, n), rng.uniform(0, w, n)
+    ends = rng.random(n) < 0.25
+    qx[ends] = np.nextafter(w, 0)
+    mx[ends] = 0.0
+    rx = (qx + ox * w) - mx
+    ry = (qy + oy * w) - my
+    d2 = rx * rx + ry * ry
+    sx = ((approx_f32(qx) + (ox.astype(np.float32) * wf).astype(np.float32)).astype(np.float32) - approx_f32(mx)).astype(np.float32)
+    sy = ((approx_f32(qy) + (oy.astype(np.float32) * wf).astype(np.float32)).astype(np.float32) - approx_f32(my)).astype(np.float32)
+    d2f = (sx * sx).astype(np.float32) + (sy * sy).astype(np.float32)
+    err = np.abs(d2f.astype(np.float64) - d2)
+    assert err.max() <= M / 2, (err.max(), M)
