@@ -297,7 +297,7 @@ __device__ __forceinline__ uint32_t try_cell_in(const Rep& rep, uint32_t sweep, 
         } else {
             np.x = __dadd_rn(me.x, step_fp64(u.x, u.y, rep.delta));
             np.y = __dadd_rn(me.y, step_fp64(u.z, u.w, rep.delta));
-            ok = np.x >= 0.0 && np.x < rep.w && np.y >= 0.0 && np.y < rep.w;
+            ok = nonneg_bits(np.x) && below_pos_bits(np.x, rep.w) && nonneg_bits(np.y) && below_pos_bits(np.y, rep.w);
         }
         // The tests run whatever the boundary test said (a warp rarely skips
         // them all), without branches: a slot that is not an occupant, or the

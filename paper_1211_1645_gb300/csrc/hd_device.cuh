@@ -177,12 +177,47 @@ __device__ __forceinline__ int find_rep(const Rep* __restrict__ reps, int R, int
     return lo;
 }
 
+// GB300's FP64 pipe is narrow, so the FP64 form does on integer units what
+// needs no rounding: the conversion of an integer of at most 53 bits, a
+// scaling by a power of two, and comparisons.  The values involved are
+// finite and never NaN.
+//
+// double(v) for 0 < |v| < 2^53 (exact): the leading one moved to bit 52 and
+// dropped, the exponent from the leading-zero count.
+__device__ __forceinline__ double exact_from_i53(int64_t v) {
+    const uint64_t s = v < 0 ? (uint64_t(1) << 63) : 0u;
+    const uint64_t a = v < 0 ? uint64_t(-v) : uint64_t(v);
+    const int lz = __clzll(static_cast<long long>(a));  // >= 11
+    const uint64_t mant = (a << (lz - 11)) & ((uint64_t(1) << 52) - 1u);
+    return __longlong_as_double(static_cast<long long>(s | (uint64_t(1023 + 63 - lz) << 52) | mant));
+}
+
+// x * 2^-53, as the FP64 multiply gives it: the exponent lowered when the
+// result stays normal (exact), the multiply itself otherwise (zero, tiny).
+__device__ __forceinline__ double scale_2m53(double x) {
+    const long long b = __double_as_longlong(x);
+    if (((b >> 52) & 0x7FF) > 53) return __longlong_as_double(b - (static_cast<long long>(53) << 52));
+    return __dmul_rn(x, 0x1p-53);
+}
+
+// x >= 0.0 (-0.0 included) and x < y for finite x and finite y > 0, on the
+// bits: a non-negative double orders as its bit pattern; a negative one
+// (sign bit set) is a negative integer, below any positive y.
+__device__ __forceinline__ bool nonneg_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == static_cast<long long>(0x8000000000000000ull);
+}
+__device__ __forceinline__ bool below_pos_bits(double x, double y) {
+    return __double_as_longlong(x) < __double_as_longlong(y);
+}
+
 // Symmetric FP64 step in (-delta, delta) from two 32-bit words: a 53-bit
-// integer k gives (2k + 1 - 2^53) * 2^-53, a set symmetric about zero.
+// integer k gives (2k + 1 - 2^53) * 2^-53, a set symmetric about zero;
+// computed as delta * v rounded once, then scaled exactly.
 __device__ __forceinline__ double step_fp64(uint32_t hi, uint32_t lo, double delta) {
     const uint64_t k = (uint64_t(hi >> 6) << 27) | uint64_t(lo >> 5);
-    const int64_t v = int64_t(2 * k + 1) - (int64_t(1) << 53);
-    return __dmul_rn(delta, double(v)) * 0x1p-53;
+    const int64_t v = int64_t(2 * k + 1) - (int64_t(1) << 53);  // odd, never 0
+    return scale_2m53(__dmul_rn(delta, exact_from_i53(v)));
 }
 
 // Move one coordinate of one disk into the next cell frame (FP64).  d is the
@@ -191,18 +226,18 @@ __device__ __forceinline__ double step_fp64(uint32_t hi, uint32_t lo, double del
 __device__ __forceinline__ void frame_change_fp64(double d, double w, double w_below, int m, int c,
                                                   double u, int& c_out, double& u_out) {
     double t = __dadd_rn(u, d);
-    if (t < 0.0) {
+    if (!nonneg_bits(t)) {
         const double v = __dadd_rn(t, w);
-        if (v < w) {
+        if (below_pos_bits(v, w)) {
             c -= 1;
             t = v;
         } else {
             t = 0.0;
         }
-    } else if (t >= w) {
+    } else if (!below_pos_bits(t, w)) {
         t = __dsub_rn(t, w);
         c += 1;
-        if (t >= w) t = w_below;
+        if (!below_pos_bits(t, w)) t = w_below;
     }
     c_out = wrap_cell(c, m);
     u_out = t;
