@@ -108,7 +108,9 @@ const char *hd_status_string(hd_status s);
  * the largest even integer with L/m >= cell_min (Sec. II.B).
  * Errors: HD_ERR_ARG if N < 2, eta <= 0, the lattice would overlap
  * (L / ceil(sqrt N) < 2 sigma), m < 4, delta < 0 or delta >= cell side, a
- * cell could hold more than 9 disks, or the fixed form would overflow int32.
+ * delta / sigma in (0, 2^-900) (the FP64 step's exact scaling assumes a
+ * normal result), a cell could hold more than 9 disks, or the fixed form
+ * would overflow int32.
  * *out receives the context (NULL on error); release it with hd_destroy.
  */
 hd_status hd_init(hd_ctx **out, int64_t N, double eta, double sigma, double delta,
@@ -318,8 +320,8 @@ hd_status hd_checkpoint_size(hd_ctx *ctx, size_t *bytes);
 
 /*
  * Maximum trial displacement per replica.  hd_set_delta sets delta[R] (sigma
- * units; 0 < delta < cell side, and at least one 2^-24 sigma step in the
- * fixed form).  hd_tune_delta runs `probes` bursts of `sweeps_per_probe`
+ * units; 2^-900 sigma <= delta < cell side, and at least one 2^-24 sigma
+ * step in the fixed form).  hd_tune_delta runs `probes` bursts of `sweeps_per_probe`
  * sweeps, measuring each replica's acceptance and scaling its delta by
  * (acceptance/target)^0.7 (clamped to a factor 1/4..4 and to the valid range)
  * toward `target` in (0, 1); the chains advance during tuning and

@@ -210,6 +210,7 @@ hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64
     while ((n - 1) * (n - 1) >= N) --n;
     if (L / double(n) < 2.0) return HD_ERR_ARG;  // the initial lattice would overlap
     const double dhat = delta / sigma;
+    if (dhat > 0.0 && dhat < 0x1p-900) return HD_ERR_ARG;  // see scale_2m53
     const int64_t W = std::llround(w * kFx);
     const int64_t D = std::llround(dhat * kFx);
     if (fixed) {
@@ -1043,7 +1044,7 @@ namespace {
 // value is out of range for the cell.
 bool set_rep_delta(hd_ctx* ctx, int r, double delta) {
     Rep& rep = ctx->reps[size_t(r)];
-    if (!(delta > 0.0)) return false;
+    if (!(delta >= 0x1p-900)) return false;  // positive, and see scale_2m53
     if (ctx->fixed) {
         const int64_t D = std::llround(delta * kFx);
         if (D < 1 || D >= rep.W) return false;

