@@ -179,19 +179,26 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         const int own = int(s_list[d] >> 4), k = int(s_list[d] & 15u);
         const P2<FIX> me = s_pos[k * nS + own];
-        const int32_t idme = s_id[k * nS + own];
+        const int32_t idme = FIX ? 0 : s_id[k * nS + own];  // the FP64 form's pair rule
         float mfx = 0.0f, mfy = 0.0f;  // FP64 form: float images of the disk's offsets
         if constexpr (!FIX) {
             mfx = approx_f32(me.x);
             mfy = approx_f32(me.y);
         }
-        for (int dcy = -RR; dcy <= RR; ++dcy) {
-            for (int dcx = -RR; dcx <= RR; ++dcx) {
+        // Each unordered pair once.  Fixed form: from the cell whose offset to
+        // the other is in the upper half of the stencil (dcy > 0, or dcy = 0
+        // and dcx > 0), or within a cell from the lower slot -- the squared
+        // distance is the same exact integer seen from either side, so the
+        // counts equal those of a lower-id rule.  FP64: from the lower id,
+        // whose rounding the oracle follows.
+        for (int dcy = FIX ? 0 : -RR; dcy <= RR; ++dcy) {
+            for (int dcx = (FIX && dcy == 0) ? 0 : -RR; dcx <= RR; ++dcx) {
                 const int sc = own + dcy * SX + dcx;
                 const int nn = s_n[sc];
-                for (int q = 0; q < nn; ++q) {
-                    const int32_t idq = s_id[q * nS + sc];
-                    if (idq <= idme) continue;
+                for (int q = (FIX && dcy == 0 && dcx == 0) ? k + 1 : 0; q < nn; ++q) {
+                    if constexpr (!FIX) {
+                        if (s_id[q * nS + sc] <= idme) continue;
+                    }
                     const P2<FIX> o = s_pos[q * nS + sc];
                     E r2;
                     if constexpr (FIX) {
