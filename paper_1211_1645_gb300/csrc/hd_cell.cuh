@@ -164,6 +164,21 @@ __device__ __forceinline__ uint32_t pick_word(const uint4& w0, const uint4& w1, 
     }
 }
 
+// The FP64 overlap test proper: the centre distance of q (its cell (ox, oy)
+// cells away) and np is at least 2 sigma.  Not inlined, so that the compiler
+// cannot turn the rarely taken call into FP64 instructions issued under a
+// false predicate on every pair test.
+static __device__ __noinline__ bool pair_clear_fp64_exact(double qx0, double qy0, int ox, int oy, double npx, double npy,
+                                                   double w) {
+    // (q + 0) is q itself for the non-negative cell offsets, so a zero cell
+    // difference skips that addition (an FP64 operation saved)
+    const double qx = ox == 0 ? qx0 : __dadd_rn(qx0, ox < 0 ? -w : w);
+    const double qy = oy == 0 ? qy0 : __dadd_rn(qy0, oy < 0 ? -w : w);
+    const double rx = __dsub_rn(qx, npx);
+    const double ry = __dsub_rn(qy, npy);
+    return !(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) < 4.0);
+}
+
 // Overlap test of a proposed position np against one occupant q whose cell is
 // (ox, oy) cells away from the moving disk's cell: true when clear (the centre
 // distance is at least 2 sigma).
@@ -191,13 +206,7 @@ __device__ __forceinline__ bool pair_clear(const P2<FIX>& q, int ox, int oy, con
         const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
         if (d2f >= rep.d2_hi) return true;
         if (d2f < rep.d2_lo) return false;
-        // (q + 0) is q itself for the non-negative cell offsets, so a zero
-        // cell difference skips that addition (an FP64 operation saved)
-        const double qx = ox == 0 ? q.x : __dadd_rn(q.x, ox < 0 ? -rep.w : rep.w);
-        const double qy = oy == 0 ? q.y : __dadd_rn(q.y, oy < 0 ? -rep.w : rep.w);
-        const double rx = __dsub_rn(qx, np.x);
-        const double ry = __dsub_rn(qy, np.y);
-        return !(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)) < 4.0);
+        return pair_clear_fp64_exact(q.x, q.y, ox, oy, np.x, np.y, rep.w);
     }
 }
 
