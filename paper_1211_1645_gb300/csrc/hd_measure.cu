@@ -134,6 +134,25 @@ __host__ __device__ constexpr size_t hist_stage_bytes(int rows, int halo, int K)
            size_t(K + 1) * 8 + size_t(K) * 4;
 }
 
+// FP64 bin of a pair (o at cell offset (dcx, dcy) from me) among the K bins
+// of squared edges edge[0..K], or -1 outside [edge_0, edge_K).  Out of line,
+// so that its FP64 instructions issue only for the pairs the float pre-test
+// leaves; the non-negative squared distance is compared through its bit
+// pattern, which orders as the value does.
+static __device__ __noinline__ int hist_bin_fp64(double ox, double oy, double mx, double my, int dcx, int dcy,
+                                                 double w, const double* edge, int K) {
+    const double rx = __dsub_rn(__dadd_rn(ox, __dmul_rn(double(dcx), w)), mx);
+    const double ry = __dsub_rn(__dadd_rn(oy, __dmul_rn(double(dcy), w)), my);
+    const long long b = __double_as_longlong(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)));
+    if (b < __double_as_longlong(edge[0]) || b >= __double_as_longlong(edge[K])) return -1;
+    int lo = 0, hi = K - 1;  // largest k with edge[k] <= r^2
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__double_as_longlong(edge[mid]) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict__ edges,
@@ -214,9 +233,9 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
                         const float sy = __fsub_rn(__fadd_rn(approx_f32(o.y), __fmul_rn(float(dcy), rep.wf)), mfy);
                         const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
                         if (d2f < rep.h_lo || d2f >= rep.h_hi) continue;
-                        const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
-                        const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
-                        r2 = __dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry));
+                        const int bin = hist_bin_fp64(o.x, o.y, me.x, me.y, dcx, dcy, rep.w, s_edge, K);
+                        if (bin >= 0) atomicAdd(&s_bins[bin], 1u);
+                        continue;
                     }
                     if (r2 < lo_edge || r2 >= hi_edge) continue;
                     int lo = 0, hi = K - 1;  // largest k with edge[k] <= r2
@@ -354,7 +373,10 @@ __global__ void __launch_bounds__(32) k_fit(const Rep* __restrict__ reps, int K,
 // ---------------------------------------------------------------------------
 template <bool FIX>
 struct Nbr {
-    using Key = std::conditional_t<FIX, long long, double>;
+    // squared distances: exact integers (fixed form), or the bit patterns of
+    // the non-negative FP64 values, which order as the values do (so the
+    // list needs no FP64 comparison)
+    using Key = long long;
     // pair offsets: 32-bit in the fixed form (the ring search never reaches
     // (RR + 1) W >= 2^31, so |r| < 2^31)
     using Off = std::conditional_t<FIX, int32_t, double>;
@@ -406,7 +428,7 @@ __device__ __forceinline__ void scan_cell(const Rep& rep, const uint8_t* __restr
         } else {
             const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
             const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
-            nb.insert(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), idq, rx, ry);
+            nb.insert(__double_as_longlong(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry))), idq, rx, ry);
         }
     }
 }
@@ -433,7 +455,7 @@ __device__ __forceinline__ bool ring_covers(const Rep& rep, const Nbr<FIX>& nb, 
         cv = c2 < cv ? c2 : cv;
         cv = c3 < cv ? c3 : cv;
         cv = c4 < cv ? c4 : cv;
-        return nb.key[5] < __dmul_rn(cv, cv);
+        return nb.key[5] < __double_as_longlong(__dmul_rn(cv, cv));
     }
 }
 
@@ -534,12 +556,12 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                                         const float sx = __fsub_rn(__fadd_rn(approx_f32(o.x), __fmul_rn(float(dcx), rep.wf)), mfx);
                                         const float sy = __fsub_rn(__fadd_rn(approx_f32(o.y), __fmul_rn(float(dcy), rep.wf)), mfy);
                                         const float d2f = __fadd_rn(__fmul_rn(sx, sx), __fmul_rn(sy, sy));
-                                        const float k5 = __fmul_ru(approx_f32(nb.key[5]), 1.0f + 0x1p-19f);
+                                        const float k5 = __fmul_ru(approx_f32(__longlong_as_double(nb.key[5])), 1.0f + 0x1p-19f);
                                         if (d2f > __fadd_ru(k5, rep.psi_m)) continue;
                                     }
                                     const double rx = __dsub_rn(__dadd_rn(o.x, __dmul_rn(double(dcx), rep.w)), me.x);
                                     const double ry = __dsub_rn(__dadd_rn(o.y, __dmul_rn(double(dcy), rep.w)), me.y);
-                                    nb.insert(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), idq, rx, ry);
+                                    nb.insert(__double_as_longlong(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry))), idq, rx, ry);
                                 }
                             }
                         }
@@ -594,8 +616,9 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                     const double c6 = __dsub_rn(__dmul_rn(c4, c2), __dmul_rn(s4, s2));
                     const double s6 = __dadd_rn(__dmul_rn(c4, s2), __dmul_rn(s4, c2));
                     const double r6 = __dmul_rn(__dmul_rn(r2, r2), r2);
-                    dr_ = __dadd_rn(dr_, __ddiv_rn(c6, r6));
-                    di = __dadd_rn(di, __ddiv_rn(s6, r6));
+                    const double inv = __ddiv_rn(1.0, r6);  // one division for both parts
+                    dr_ = __dadd_rn(dr_, __dmul_rn(c6, inv));
+                    di = __dadd_rn(di, __dmul_rn(s6, inv));
                 }
                 pre = __ddiv_rn(dr_, 6.0);
                 pim = __ddiv_rn(di, 6.0);
