@@ -264,7 +264,7 @@ __device__ __forceinline__ uint32_t try_cell_in(const Rep& rep, uint32_t sweep, 
         uint4 w0, w1 = make_uint4(0, 0, 0, 0);
         if constexpr (FIX) {
             w0 = make_uint4(u0.z, u0.w, 0u, 0u);
-            if (CAP > 3 && n > 3) {  // n <= CAP: the two-slot path has no such cell
+            if (n > 3) {
                 const uint4 a = philox(sweep, 0u, cl, kTagShuffle, rep.key0, rep.key1);
                 w0.z = a.x;
                 w0.w = a.y;
