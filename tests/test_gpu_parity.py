@@ -23,6 +23,9 @@ CASES = {
     "two_trials_wide_cells": dict(N=1000, eta=0.716, delta=0.1, seed=6, cell_min=2.2),
     "cap9_cells": dict(N=300, eta=0.50, delta=0.4, seed=9, cell_min=3.0),
     "two_disks": dict(N=2, eta=2 * math.pi / 100, delta=1.0, seed=4),
+    # square lattice 0.007 sigma from contact with tiny steps: many pairs land
+    # near contact, where the FP64 form's float pre-test hands over to FP64
+    "near_contact_dense": dict(N=1024, eta=0.78, delta=0.004, seed=12),
 }
 
 
