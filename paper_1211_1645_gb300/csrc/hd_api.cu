@@ -116,6 +116,7 @@ struct hd_ctx {
     hd::LaunchCfg cfg() const {
         hd::LaunchCfg c;
         c.reps = reps_d;
+        c.rep0 = reps.data();
         c.R = R;
         c.cap = cap;
         c.fixed = fixed;
@@ -1061,6 +1062,7 @@ bool set_rep_delta(hd_ctx* ctx, int r, double delta) {
 hd_status upload_reps(hd_ctx* ctx) {
     HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
     HD_CK(ctx, cudaMemcpy(ctx->reps_d, ctx->reps.data(), sizeof(Rep) * size_t(ctx->R), cudaMemcpyHostToDevice));
+    drop_graphs(ctx);  // captured launches may hold the replica constants by value
     return HD_OK;
 }
 }  // namespace

@@ -20,6 +20,7 @@ struct CellBufs {
 
 struct LaunchCfg {
     const Rep* reps;   // device array [R]
+    const Rep* rep0;   // host copy of replica 0 (passed by value to the hot kernels when R == 1)
     int R;
     int cap;           // 4 or 9
     bool fixed;        // fixed-point form
