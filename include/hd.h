@@ -119,7 +119,8 @@ hd_status hd_init(hd_ctx **out, int64_t N, double eta, double sigma, double delt
 /*
  * Create R independent chains in one context (the equation-of-state scan of
  * Sec. IV.A as one batch).  N[R], eta[R], delta[R], seed[R] are per replica;
- * sigma and opts are shared.  Same errors as hd_init, per replica.
+ * sigma and opts are shared.  Same errors as hd_init, per replica, and
+ * HD_ERR_ARG unless 1 <= R <= 65535.
  */
 hd_status hd_batch_init(hd_ctx **out, int32_t R, const int64_t *N, const double *eta, double sigma,
                         const double *delta, const uint64_t *seed, const hd_opts *opts);

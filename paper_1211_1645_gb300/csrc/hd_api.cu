@@ -81,6 +81,8 @@ struct hd_ctx {
     double2* psi_part = nullptr;
     double* psi_res = nullptr;
     double* xy = nullptr;
+    uint16_t* rep_of_act = nullptr;   // replica of each active-cell-grid block
+    uint16_t* rep_of_cell = nullptr;  // replica of each whole-cell-grid block
     cudaStream_t stream = nullptr;
     hd_status sticky = HD_OK;
     std::vector<int64_t> sweeps;
@@ -117,6 +119,8 @@ struct hd_ctx {
         hd::LaunchCfg c;
         c.reps = reps_d;
         c.rep0 = reps.data();
+        c.rep_of_act = rep_of_act;
+        c.rep_of_cell = rep_of_cell;
         c.R = R;
         c.cap = cap;
         c.fixed = fixed;
@@ -521,7 +525,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
                         const double* delta, const uint64_t* seed, const hd_opts* opts_in) {
     if (!out) return HD_ERR_ARG;
     *out = nullptr;
-    if (R < 1 || !N || !eta || !delta || !seed) return HD_ERR_ARG;
+    if (R < 1 || R > 65535 || !N || !eta || !delta || !seed) return HD_ERR_ARG;
     hd_opts o;
     hd_default_opts(&o);
     if (opts_in) {
@@ -672,6 +676,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ok = ok && dev_alloc(ctx, &ctx->psi_local, size_t(ctx->Ntot));
     ok = ok && dev_alloc(ctx, &ctx->psi_part, size_t(ctx->blocks_t32));
     ok = ok && dev_alloc(ctx, &ctx->psi_res, size_t(2 * R));
+    ok = ok && dev_alloc(ctx, &ctx->rep_of_act, size_t(ctx->blocks_act));
+    ok = ok && dev_alloc(ctx, &ctx->rep_of_cell, size_t(ctx->blocks_cell));
     ok = ok && dev_alloc(ctx, &ctx->xy, size_t(2 * ctx->Ntot));
     if (!ok) {
         free_ctx(ctx);
@@ -686,8 +692,19 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         const long long xf = (1LL << 25) + (long long)k * DR;
         ef[size_t(k)] = xf * xf;
     }
+    // block -> replica tables of the two cell grids (R <= 65535 replicas)
+    std::vector<uint16_t> ra(size_t(ctx->blocks_act)), rc(size_t(ctx->blocks_cell));
+    for (int r = 0; r < R; ++r) {
+        const Rep& rep = ctx->reps[size_t(r)];
+        const int ea = r + 1 < R ? ctx->reps[size_t(r + 1)].blk_act : ctx->blocks_act;
+        const int ec = r + 1 < R ? ctx->reps[size_t(r + 1)].blk_cell : ctx->blocks_cell;
+        for (int b = rep.blk_act; b < ea; ++b) ra[size_t(b)] = uint16_t(r);
+        for (int b = rep.blk_cell; b < ec; ++b) rc[size_t(b)] = uint16_t(r);
+    }
     bool cu = cudaMemcpy(ctx->reps_d, ctx->reps.data(), sizeof(Rep) * size_t(R), cudaMemcpyHostToDevice) == cudaSuccess;
     cu = cu && cudaMemcpy(ctx->edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    cu = cu && cudaMemcpy(ctx->rep_of_act, ra.data(), ra.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) == cudaSuccess;
+    cu = cu && cudaMemcpy(ctx->rep_of_cell, rc.data(), rc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) == cudaSuccess;
     cu = cu && cudaMemcpy(ctx->edgesF, ef.data(), ef.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess;
     cu = cu && cudaMemset(ctx->sweep_ctr, 0, sizeof(uint64_t) * size_t(R)) == cudaSuccess;
     cu = cu && cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * size_t(2 * R)) == cudaSuccess;

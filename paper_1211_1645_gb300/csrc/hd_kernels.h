@@ -21,6 +21,8 @@ struct CellBufs {
 struct LaunchCfg {
     const Rep* reps;   // device array [R]
     const Rep* rep0;   // host copy of replica 0 (passed by value to the hot kernels when R == 1)
+    const uint16_t* rep_of_act;   // replica of each block of the active-cell grid (R > 1)
+    const uint16_t* rep_of_cell;  // replica of each block of the whole-cell grid (R > 1)
     int R;
     int cap;           // 4 or 9
     bool fixed;        // fixed-point form

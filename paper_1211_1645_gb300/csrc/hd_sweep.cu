@@ -84,15 +84,17 @@ __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__
 // both and then the slot claims of both before it waits on any, so the two
 // latency chains (loads, then claims, then stores) overlap.
 // ONE: a single replica, whose constants come by value in rep1 (kernel
-// parameters, read as constant operands) instead of from reps.
+// parameters, read as constant operands) instead of from reps; otherwise the
+// block's replica comes from rep_of (one entry per block).
 template <bool FIX, int CAP, bool ONE>
 __global__ void __launch_bounds__(256)
-k_rebuild(const Rep* __restrict__ reps, int R, const Rep rep1, const Frame* __restrict__ table, int j,
+k_rebuild(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const Rep rep1,
+          const Frame* __restrict__ table, int j,
           uint8_t* __restrict__ cnt_o, const P2<FIX>* __restrict__ pos_o, const int32_t* __restrict__ pid_o,
           uint8_t* __restrict__ cnt_n, P2<FIX>* __restrict__ pos_n, int32_t* __restrict__ pid_n,
           int* __restrict__ err) {
     pdl_begin();
-    const int r = ONE ? 0 : find_rep<kGridCell>(reps, R, blockIdx.x);
+    const int r = ONE ? 0 : int(rep_of[blockIdx.x]);
     const Rep rep = ONE ? rep1 : reps[r];
     const int m = rep.m;
     const uint32_t mm = uint32_t(m) * uint32_t(m);
@@ -221,14 +223,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <bool FIX, int CAP, int NTC, bool ONE>
 __global__ void __launch_bounds__(256)
-k_pass(const Rep* __restrict__ reps, int R, const Rep rep1, const Frame* __restrict__ table, int j, int p,
+k_pass(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const Rep rep1,
+       const Frame* __restrict__ table, int j, int p,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
     pdl_begin();
     extern __shared__ __align__(16) unsigned char s_raw[];
     int2* s_nbr = reinterpret_cast<int2*>(s_raw);
     P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + (FIX ? size_t(blockDim.x) * kNbrStride * sizeof(int2) : 0));
     int32_t* s_crowd_id = reinterpret_cast<int32_t*>(s_crowd + size_t(blockDim.x) * CAP);
-    const int r = ONE ? 0 : find_rep<kGridAct>(reps, R, blockIdx.x);
+    const int r = ONE ? 0 : int(rep_of[blockIdx.x]);
     const Rep rep = ONE ? rep1 : reps[r];
     const int m = rep.m, hm = rep.hm;
     const uint32_t a = uint32_t(blockIdx.x - rep.blk_act) * blockDim.x + threadIdx.x;
@@ -406,12 +409,12 @@ cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t*
 template <bool FIX, int CAP>
 static cudaError_t rebuild_t(const LaunchCfg& c, const Frame* table, int j, CellBufs a, CellBufs b, int* err) {
     if (c.R == 1)
-        return launch_k(k_rebuild<FIX, CAP, true>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps, c.R,
-                        *c.rep0, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt, (P2<FIX>*)b.pos,
-                        b.pid, err);
-    return launch_k(k_rebuild<FIX, CAP, false>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps, c.R,
-                    Rep{}, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt, (P2<FIX>*)b.pos, b.pid,
-                    err);
+        return launch_k(k_rebuild<FIX, CAP, true>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps,
+                        c.rep_of_cell, *c.rep0, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
+                        (P2<FIX>*)b.pos, b.pid, err);
+    return launch_k(k_rebuild<FIX, CAP, false>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps,
+                    c.rep_of_cell, Rep{}, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
+                    (P2<FIX>*)b.pos, b.pid, err);
 }
 
 cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to, int* err) {
@@ -431,10 +434,12 @@ static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, 
                              int(pass_smem<FIX, CAP>(256)));
     });
     if (c.R == 1)
-        return launch_k(k_pass<FIX, CAP, NTC, true>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R,
-                        *c.rep0, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
-    return launch_k(k_pass<FIX, CAP, NTC, false>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps, c.R,
-                    Rep{}, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid, counters);
+        return launch_k(k_pass<FIX, CAP, NTC, true>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps,
+                        c.rep_of_act, *c.rep0, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid,
+                        counters);
+    return launch_k(k_pass<FIX, CAP, NTC, false>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps,
+                    c.rep_of_act, Rep{}, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid,
+                    counters);
 }
 
 template <bool FIX, int CAP>
