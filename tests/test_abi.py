@@ -73,6 +73,21 @@ def test_invalid_arguments_rejected_on_host(hdlib, N, eta, sigma, delta, kw):
     assert not h.value
 
 
+def test_batch_replica_count_bounds(hdlib):
+    """1 <= R <= 65535 (the per-block replica tables hold 16-bit indices);
+    the count is checked before any per-replica array is read."""
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    one_n = (ctypes.c_int64 * 1)(256)
+    one_d = (ctypes.c_double * 1)(0.7)
+    one_s = (ctypes.c_uint64 * 1)(1)
+    h = ctypes.c_void_p()
+    for R in (0, 65536):
+        st = lib.hd_batch_init(ctypes.byref(h), ctypes.c_int32(R), one_n, one_d, ctypes.c_double(1.0), one_d, one_s,
+                               None)
+        assert st == b.HD_ERR_ARG and not h.value
+
+
 def test_null_context_calls(hdlib):
     hd, lib = hdlib
     from paper_1211_1645_gb300 import hd as b

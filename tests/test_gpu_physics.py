@@ -181,3 +181,22 @@ def test_table2_psi6_correlation_time(hd):
           f"{s_per_tau:.1f} s of GPU time per tau for the four replicas")
     assert 8e5 / 4 < tau_disp < 8e5 * 4
     g.close()
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_set_delta_reaches_captured_steps(hd, form):
+    """A single replica's constants enter the sweep launches by value, so a
+    changed delta must reach the graph-captured steps too: graph steps with
+    a delta change in between equal direct sweeps with the same change."""
+    a = hd.HardDisks(1000, 0.65, 0.1, 6, precision=form)
+    b = hd.HardDisks(1000, 0.65, 0.1, 6, precision=form)
+    a.run(1, 7, False)
+    b.sweep(7)
+    a.set_delta(0.25)
+    b.set_delta(0.25)
+    a.run(2, 7, False)
+    b.sweep(14)
+    assert np.array_equal(a.positions(), b.positions())
+    assert [x.tolist() for x in a.stats()] == [x.tolist() for x in b.stats()]
+    a.close()
+    b.close()
