@@ -20,7 +20,10 @@ constexpr int kMaxFitBins = 512;
 
 // ---------------------------------------------------------------------------
 // Contact-shell histogram: unordered pairs with 2 <= r < 2 + K dr, binned by
-// comparing r^2 with squared bin edges; each pair is seen from its lower id.
+// comparing r^2 with squared bin edges; each pair is counted once, from its
+// lower id (k_hist_global; the FP64 form of k_hist_tile) or, in the fixed
+// form of k_hist_tile, from the upper half of the stencil (the same exact
+// squared distance from either side, so the same counts).
 // One thread per cell scans the (2R+1)^2 stencil; counts gather in a shared
 // histogram and are flushed with one atomic per non-empty bin and block.
 // k_hist_global reads the stencil from global memory (any reach R);
