@@ -12,6 +12,7 @@
 #include "hd_kernels.h"
 #include "hd_analysis.h"
 #include "hd_bin.h"
+#include "hd_bounds.h"
 
 using hd::CellBufs;
 using hd::Frame;
@@ -159,44 +160,22 @@ bool dev_alloc(hd_ctx* ctx, T** p, size_t count) {
     return true;
 }
 
-// Bounds of the FP64 form's float pre-test of a pair (pair_clear).  With
-// t = 2^-20 (the relative error of approx_f32) and u = 2^-24 (float
-// rounding), and |q| < w, |cell offset| <= w, |np| < w + delta,
-// |rx| <= R = 2w + delta: the float difference errs by at most
-// E = t (2w + delta) + u (3w + R), the float square sum by
-// 4 R E + 2 E^2 + 4 u (R + E)^2, and the FP64 square sum by less than
-// 16 2^-53 R^2.  Twice their sum, M, brackets (2 sigma)^2 = 4: a float
-// estimate at or above 4 + M (below 4 - M) certifies a clear pair (an
-// overlap) exactly as the FP64 test would.
+// Float pre-test bounds of the FP64 form (hd_bounds.h): the cell side in
+// float and floats bracketing (2 sigma)^2 = 4 by the pair margin.
 void set_f32_bounds(Rep& r) {
-    const double t = std::ldexp(1.0, -20), u = std::ldexp(1.0, -24);
-    const double w = r.w, d = r.delta, R = 2.0 * w + d;
-    const double E = t * (2.0 * w + d) + u * (3.0 * w + R);
-    const double M = 2.0 * (4.0 * R * E + 2.0 * E * E + 4.0 * u * (R + E) * (R + E) + 16.0 * std::ldexp(1.0, -53) * R * R);
-    r.wf = float(w);
+    const double M = hd::pair_f32_margin(r.w, r.delta);
+    r.wf = float(r.w);
     r.d2_lo = std::nextafter(float(4.0 - M), -HUGE_VALF);
     r.d2_hi = std::nextafter(float(4.0 + M), HUGE_VALF);
 }
 
-// The same bound for the FP64 contact histogram's float pre-test
-// (k_hist_tile): a pair H = hist_R cells apart at most, so |rx| <= R =
-// (H + 1) w, with the float offset dcx wf (rounded product) added to the
-// neighbour's coordinate.  The float difference errs by at most
-// E = 2 t w + u w (4H + 2); a pair whose float estimate of r^2 lies outside
-// [edge_0 - M, edge_K + M) is outside the histogram's range in FP64.
-double cells_f32_margin(double w, int H) {
-    const double t = std::ldexp(1.0, -20), u = std::ldexp(1.0, -24);
-    const double R = (double(H) + 1.0) * w;
-    const double E = 2.0 * t * w + u * w * (4.0 * double(H) + 2.0);
-    return 2.0 * (4.0 * R * E + 2.0 * E * E + 4.0 * u * (R + E) * (R + E) + 16.0 * std::ldexp(1.0, -53) * R * R);
-}
-
-// The histogram bounds, and the psi_6 margin (candidates two cells apart).
+// The histogram's range [e0, eK) widened by the margin of pairs hist_R cells
+// apart, and the psi_6 margin (candidates two cells apart).
 void set_hist_f32_bounds(Rep& r, double e0, double eK) {
-    const double M = cells_f32_margin(r.w, r.hist_R);
+    const double M = hd::cells_f32_margin(r.w, r.hist_R);
     r.h_lo = std::nextafter(float(e0 - M), -HUGE_VALF);
     r.h_hi = std::nextafter(float(eK + M), HUGE_VALF);
-    r.psi_m = std::nextafter(float(cells_f32_margin(r.w, 2)), HUGE_VALF);
+    r.psi_m = std::nextafter(float(hd::cells_f32_margin(r.w, 2)), HUGE_VALF);
 }
 
 // Geometry of one chain (Sec. II.A, II.B).  Lengths in units of sigma.

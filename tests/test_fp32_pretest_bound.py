@@ -105,3 +105,34 @@ def test_histogram_float_estimate_within_half_margin(w, H):
     d2f = (sx * sx).astype(np.float32) + (sy * sy).astype(np.float32)
     err = np.abs(d2f.astype(np.float64) - d2)
     assert err.max() <= M / 2, (err.max(), M)
+
+
+def test_library_margins_are_the_checked_bounds(tmp_path):
+    """The margins the library computes (hd_bounds.h, compiled here as host
+    C++) are the ones whose claim the tests above check."""
+    import os
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "margins.cpp"
+    src.write_text(
+        '#include <cstdio>\n#include "hd_bounds.h"\n'
+        "int main() {\n"
+        "  const double w[] = {2.0008917450904846, 2.0122, 3.0, 7.9};\n"
+        "  const double d[] = {0.1, 0.258, 1.4, 7.8};\n"
+        "  const int H[] = {2, 2, 4, 1};\n"
+        "  for (int i = 0; i < 4; ++i)\n"
+        '    std::printf("%.17g %.17g\\n", hd::pair_f32_margin(w[i], d[i]), hd::cells_f32_margin(w[i], H[i]));\n'
+        "}\n")
+    exe = tmp_path / "margins"
+    subprocess.run([gxx, "-std=c++17", "-O0", "-ffp-contract=off", "-I",
+                    os.path.join(root, "paper_1211_1645_gb300", "csrc"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = [float(x) for x in out]
+    cases = [(2.0008917450904846, 0.1, 2), (2.0122, 0.258, 2), (3.0, 1.4, 4), (7.9, 7.8, 1)]
+    for k, (w, d, H) in enumerate(cases):
+        assert got[2 * k] == pytest.approx(margin(w, d), rel=1e-14)
+        assert got[2 * k + 1] == pytest.approx(hist_margin(w, H), rel=1e-14)
