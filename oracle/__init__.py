@@ -28,11 +28,13 @@ shells and its rotation / reflection covariance; brute-force neighbour and
 pair enumeration; the autocorrelation of constant and uniformly rotating
 series (exact), of a complex AR(1) process (rho^dt) and an exact exponential
 (tau); the coarse field of uniform psi_j, of one sampling area (= Psi_6),
-of disks on sampling-area edges, and against a per-area loop.
+of disks on sampling-area edges, and against a per-area loop; the global
+Psi_6 against exact rational arithmetic and under reordering of the disks.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -88,7 +90,7 @@ def _load():
         lib.hdo_frame.argtypes = [P, P, P, P]
         lib.hdo_histogram.argtypes = [P, c.c_int, c.c_double, c.c_int, P]
         lib.hdo_histogram.restype = c.c_int
-        lib.hdo_psi6.argtypes = [P, c.c_int, P, P]
+        lib.hdo_psi6.argtypes = [P, c.c_int, P]
         lib.hdo_psi6.restype = c.c_int
         lib.hdo_philox4x32_10.argtypes = [P, P, P]
         _lib = lib
@@ -177,18 +179,29 @@ class OracleChain:
         return out
 
     def psi6(self, brute: bool = False):
+        """Local psi_j (Eq. 8) by disk id, and the global Psi_6 = (1/N) sum_j
+        psi_j: each part's sum over the disks exactly rounded to double
+        (math.fsum), then divided by N."""
         loc = np.empty((self.N, 2), np.float64)
-        glob = np.empty(2, np.float64)
-        rc = _load().hdo_psi6(self._h, int(bool(brute)), _ptr(loc), _ptr(glob))
+        rc = _load().hdo_psi6(self._h, int(bool(brute)), _ptr(loc))
         if rc != 0:
             raise ValueError(f"psi6 neighbour search failed (status {rc})")
-        return loc[:, 0] + 1j * loc[:, 1], complex(glob[0], glob[1])
+        return loc[:, 0] + 1j * loc[:, 1], psi6_mean(loc[:, 0] + 1j * loc[:, 1])
 
     def realised_dr(self, dr: float) -> float:
         """Bin width actually used: dr itself (FP64) or dr on the 2^-24 grid."""
         if self.form == "fixed":
             return float(np.round(dr * FX_SCALE)) / FX_SCALE
         return float(dr)
+
+
+def psi6_mean(psi_local) -> complex:
+    """Global Psi_6 = (1/N) sum_j psi_j (Eq. 8).  The sum of each part is
+    exactly rounded to double (math.fsum: independent of summation order),
+    then divided by N once."""
+    z = np.asarray(psi_local, dtype=np.complex128).ravel()
+    n = float(z.size)
+    return complex(math.fsum(z.real.tolist()) / n, math.fsum(z.imag.tolist()) / n)
 
 
 def g_of_r(counts, N: int, L: float, dr: float):

@@ -662,14 +662,14 @@ static void make_cand(const hdo_state *s, int64_t i, int64_t j, int dcx, int dcy
  * z = rx + i ry, so no trigonometric function enters.  Neighbours are summed
  * in ascending (r^2, id).  The FP64 form computes in double; the fixed form
  * takes the exact integer vector, scales it by 2^-24 into float and computes
- * in float.  Global Psi_6 = (1/N) sum_j psi_j in double.
+ * in float.  The global Psi_6 = (1/N) sum_j psi_j is formed from this field
+ * by the Python layer (an exactly rounded sum, then one division by N).
  * brute != 0 scans all disks instead of expanding cell rings.
  */
-int hdo_psi6(const hdo_state *s, int brute, double *local, double *glob)
+int hdo_psi6(const hdo_state *s, int brute, double *local)
 {
     int m = s->m;
     if (s->N < 7) return HDO_ERR_REACH;
-    double sum_re = 0.0, sum_im = 0.0;
     for (int64_t i = 0; i < s->N; ++i) {
         nbr_t best[6], cand;
         int nb = 0;
@@ -759,12 +759,9 @@ int hdo_psi6(const hdo_state *s, int brute, double *local, double *glob)
             pre = (double)(sr / 6.0f);
             pim = (double)(si / 6.0f);
         }
-        if (local) { local[2 * i] = pre; local[2 * i + 1] = pim; }
-        sum_re += pre;
-        sum_im += pim;
+        local[2 * i] = pre;
+        local[2 * i + 1] = pim;
     }
-    glob[0] = sum_re / (double)s->N;
-    glob[1] = sum_im / (double)s->N;
     return HDO_OK;
 }
 

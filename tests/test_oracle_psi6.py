@@ -83,3 +83,33 @@ def test_ring_search_equals_brute(oracle_mod, form, eta):
         b, gb = o.psi6(brute=True)
         assert np.array_equal(a, b) and ga == gb
         assert np.all(np.abs(a) <= 1 + 1e-6)
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_global_is_exactly_rounded_mean(oracle_mod, form):
+    """Psi_6 = (1/N) sum_j psi_j (Eq. 8) with each part's sum rounded once:
+    checked against exact rational arithmetic on a liquid state, and
+    unchanged (bit for bit) when the disks are summed in another order."""
+    from fractions import Fraction
+    o = _liquid(oracle_mod, form)
+    loc, glob = o.psi6()
+    N = loc.size
+    for part, got in ((loc.real, glob.real), (loc.imag, glob.imag)):
+        exact = sum((Fraction(float(v)) for v in part), Fraction(0))
+        assert got == float(exact) / N
+    perm = np.random.default_rng(1).permutation(N)
+    assert oracle_mod.psi6_mean(loc[perm]) == glob
+
+
+def test_exact_mean_keeps_small_terms():
+    """A running double sum drops 2^20 terms of 2^-60 added to 1; the
+    exactly rounded sum keeps them: 1 + 2^-40."""
+    import oracle
+    z = np.array([1.0] + [2.0 ** -60] * (1 << 20)) * (1 - 1j)
+    n = z.size
+    got = oracle.psi6_mean(z)
+    assert got == complex((1 + 2.0 ** -40) / n, -(1 + 2.0 ** -40) / n)
+    naive = 0.0
+    for v in z.real[:1000]:
+        naive += v
+    assert naive == 1.0
