@@ -8,7 +8,9 @@
  * hd_status and never aborts the process.  Output-returning calls synchronise
  * the context's stream.  A CUDA failure or a device-side error flag leaves the
  * context in a sticky error state: every later call except hd_destroy returns
- * HD_ERR_STATE.
+ * HD_ERR_STATE.  After HD_ERR_TIMEOUT in particular, a bulk copy that gave up
+ * waiting may still have been in flight: destroy the context and treat what it
+ * held on the device as lost.
  *
  * Units: sigma is the disk radius.  Positions are in [0, L) x [0, L) with
  * periodic boundaries; L = sqrt(N pi sigma^2 / eta) (Sec. II.A).
@@ -94,10 +96,12 @@ typedef struct hd_geometry {
     int64_t sweeps;     /* sweeps done                                            */
 } hd_geometry;
 
-/* Fill *o with the defaults. */
+/* Fill *o with the defaults of each field (the cell side of Sec. II.B, the
+ * trials per cell of Sec. II.B, the histogram of Sec. II.C.1). */
 void hd_default_opts(hd_opts *o);
 
-/* Human-readable name of a status code (static storage). */
+/* Human-readable name of a status code (static storage).  Bookkeeping of the
+ * library: the paper has no counterpart. */
 const char *hd_status_string(hd_status s);
 
 /*
@@ -125,11 +129,13 @@ hd_status hd_init(hd_ctx **out, int64_t N, double eta, double sigma, double delt
 hd_status hd_batch_init(hd_ctx **out, int32_t R, const int64_t *N, const double *eta, double sigma,
                         const double *delta, const uint64_t *seed, const hd_opts *opts);
 
-/* Release all device and host memory of the context.  NULL is allowed. */
+/* Release all device and host memory of the context.  NULL is allowed.
+ * Bookkeeping of the library: the paper has no counterpart. */
 hd_status hd_destroy(hd_ctx *ctx);
 
 /* Launch all later work of the context on this CUDA stream (a cudaStream_t
- * passed as void*; NULL = the legacy default stream). */
+ * passed as void*; NULL = the legacy default stream).  Bookkeeping of the
+ * library: the paper has no counterpart. */
 hd_status hd_set_stream(hd_ctx *ctx, void *stream);
 
 /*
@@ -167,16 +173,21 @@ hd_status hd_pressure(hd_ctx *ctx, double *betaP_over_rho, double *g_contact, ui
  */
 hd_status hd_psi6(hd_ctx *ctx, double *re, double *im, double *local);
 
-/* Global positions (host, caller-owned, [2 * sum N_r] interleaved x, y in
- * [0, L), by disk id).  Synchronises. */
+/*
+ * The configuration: the disk centres in the periodic L x L box of Sec. II.A,
+ * as global coordinates in [0, L) (the cell frame of Sec. II.B undone).
+ *   hd_positions         host array, caller-owned, [2 * sum N_r] interleaved
+ *                        x, y by disk id.  Synchronises.
+ *   hd_positions_device  the same into a device buffer of 2 * sum N_r doubles
+ *                        (caller-owned).  Asynchronous.
+ */
 hd_status hd_positions(hd_ctx *ctx, double *xy);
-
-/* Same, into a device buffer of 2 * sum N_r doubles.  Asynchronous. */
 hd_status hd_positions_device(hd_ctx *ctx, double *xy_device);
 
 /*
- * Replace all positions (host, [2 * sum N_r], periodic images allowed; pinned
- * memory gives the fastest copy).  The positions are copied to the device
+ * Replace all positions of the configuration (Sec. II.A) (host,
+ * [2 * sum N_r], periodic images allowed; pinned memory gives the fastest
+ * copy).  The positions are copied to the device
  * and binned there into the unshifted cell frame; counters and the sweep
  * index are kept.  Overlapping input is accepted (measurements then count
  * it); the fixed form rounds to the 2^-24 sigma grid.  Synchronises.
@@ -185,15 +196,19 @@ hd_status hd_positions_device(hd_ctx *ctx, double *xy_device);
  */
 hd_status hd_set_positions(hd_ctx *ctx, const double *xy);
 
-/* Attempted and accepted trial moves since creation, per replica [R].
+/* Attempted and accepted trial moves since creation, per replica [R] (the
+ * trial moves of Sec. II.B; Table II counts displacements per disk).
  * Attempts count every trial, including moves rejected at the cell
- * boundary.  Synchronises. */
+ * boundary.  Host arrays, either may be NULL.  Synchronises. */
 hd_status hd_stats(hd_ctx *ctx, uint64_t *attempts, uint64_t *accepts);
 
-/* Geometry of replica r. */
+/* Geometry of replica r: box and packing fraction (Sec. II.A, Eq. 1), cell
+ * grid (Sec. II.B), histogram bin width (Sec. II.C.1).  HD_ERR_ARG unless
+ * 0 <= r < R. */
 hd_status hd_get_geometry(hd_ctx *ctx, int32_t r, hd_geometry *g);
 
-/* Number of replicas of the context. */
+/* Number of replicas of the context (independent chains of the
+ * equation-of-state scan, Sec. IV.A); 0 for NULL. */
 int32_t hd_replicas(const hd_ctx *ctx);
 
 /*
@@ -209,14 +224,15 @@ int32_t hd_replicas(const hd_ctx *ctx);
  */
 hd_status hd_run(hd_ctx *ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure);
 
-/* Capacity of the measurement series in steps [4096, allocated by the first
- * measuring hd_run]; reserving clears the series.  A full series keeps its
- * first entries and drops later ones. */
+/* Capacity of the measurement series of hd_run (pressure, Sec. II.C.1, and
+ * Psi_6, Sec. III) in steps [4096, allocated by the first measuring hd_run];
+ * reserving clears the series.  A full series keeps its first entries and
+ * drops later ones. */
 hd_status hd_series_reserve(hd_ctx *ctx, int64_t steps);
 
-/* Copy up to max_steps recorded steps to out[n][R][4] = (beta P / rho,
- * g(2 sigma+), Re Psi_6, Im Psi_6); *n_steps receives the number copied.
- * Synchronises. */
+/* Copy up to max_steps recorded steps to out[n][R][4] = (beta P / rho of
+ * Eq. 4, g(2 sigma+), Re and Im Psi_6 of Eq. 8); *n_steps receives the
+ * number copied.  Synchronises. */
 hd_status hd_series(hd_ctx *ctx, int64_t *n_steps, double *out, int64_t max_steps);
 
 /*
@@ -287,7 +303,7 @@ hd_status hd_positional_q0(hd_ctx *ctx, int32_t half_width, int32_t *hk0, double
 hd_status hd_positional_field(hd_ctx *ctx, const int32_t *hk0, int32_t bins, double *field);
 
 /*
- * Positional correlation function (Sec. IV.C, Eq. 12):
+ * Positional correlation function (Sec. IV.D, Eq. 12):
  * C(r_k) = < exp(i q_0 . (x_n - x_m)) > over the ordered pairs n != m whose
  * minimum-image separation d (from the global positions,
  * d = x_m - x_n - L rint((x_m - x_n) / L), d^2 = dx dx + dy dy) satisfies
@@ -300,7 +316,8 @@ hd_status hd_positional_field(hd_ctx *ctx, const int32_t *hk0, int32_t bins, dou
  */
 hd_status hd_positional_corr(hd_ctx *ctx, const int32_t *hk0, int32_t nr, double dr, double *C);
 
-/* Forget the recorded steps (asynchronous). */
+/* Forget the recorded steps of the series of Eq. 4 and Eq. 8 values
+ * (asynchronous). */
 hd_status hd_series_clear(hd_ctx *ctx);
 
 /*
@@ -318,21 +335,24 @@ hd_status hd_series_clear(hd_ctx *ctx);
  *                       measurement series is kept.  Synchronises.
  */
 hd_status hd_checkpoint_size(hd_ctx *ctx, size_t *bytes);
+hd_status hd_checkpoint(hd_ctx *ctx, void *buf, size_t bytes);
+hd_status hd_restore(hd_ctx *ctx, const void *buf, size_t bytes);
 
 /*
- * Maximum trial displacement per replica.  hd_set_delta sets delta[R] (sigma
- * units; 2^-900 sigma <= delta < cell side, and at least one 2^-24 sigma
- * step in the fixed form).  hd_tune_delta runs `probes` bursts of `sweeps_per_probe`
- * sweeps, measuring each replica's acceptance and scaling its delta by
- * (acceptance/target)^0.7 (clamped to a factor 1/4..4 and to the valid range)
- * toward `target` in (0, 1); the chains advance during tuning and
- * delta is frozen afterwards, so production sweeps keep detailed balance.
- * delta_out[R] (nullable) receives the tuned values.  Synchronises.
+ * Maximum trial displacement per replica: the delta of the trial moves of
+ * Sec. II.B (Sec. III runs each algorithm at its optimal parameters).
+ *   hd_set_delta   sets delta[R] (sigma units; 2^-900 sigma <= delta < cell
+ *                  side, and at least one 2^-24 sigma step in the fixed form).
+ *   hd_tune_delta  runs `probes` bursts of `sweeps_per_probe` sweeps,
+ *                  measuring each replica's acceptance and scaling its delta
+ *                  by (acceptance/target)^0.7 (clamped to a factor 1/4..4 and
+ *                  to the valid range) toward `target` in (0, 1); the chains
+ *                  advance during tuning and delta is frozen afterwards, so
+ *                  production sweeps keep detailed balance.  delta_out[R]
+ *                  (nullable) receives the tuned values.  Synchronises.
  */
 hd_status hd_set_delta(hd_ctx *ctx, const double *delta);
 hd_status hd_tune_delta(hd_ctx *ctx, double target, int32_t sweeps_per_probe, int32_t probes, double *delta_out);
-hd_status hd_checkpoint(hd_ctx *ctx, void *buf, size_t bytes);
-hd_status hd_restore(hd_ctx *ctx, const void *buf, size_t bytes);
 
 /*
  * Global Psi_6 = (1/N) sum_j psi_j from a per-disk field that the caller
@@ -341,18 +361,24 @@ hd_status hd_restore(hd_ctx *ctx, const void *buf, size_t bytes);
  * at this point: inside a CUDA stream capture, under a framework that owns
  * every allocation, or in a loop where an allocation could block or fail.
  * The paper has no counterpart; it is a deployment variant of the reduction
- * behind hd_psi6.
- *   psi_local_device  device array of N (Re, Im) double pairs, by disk id
+ * behind hd_psi6, with the same exact sum, so on the same field it returns
+ * hd_psi6's value bit for bit.
+ *   psi_local_device  device array of N (Re, Im) double pairs, by disk id,
+ *                     8-byte aligned (HD_ERR_ARG otherwise)
  *   N                 1 <= N <= 16,777,216 (4096 blocks of 4096 values);
  *                     larger N returns HD_ERR_ARG
- *   out_device        device array of 2 doubles receiving (Re, Im)
+ *   out_device        device array of 2 doubles receiving (Re, Im), 8-byte
+ *                     aligned
  *   stream            cudaStream_t as void* (NULL: legacy default stream)
  * The call allocates and frees nothing: its block partial sums live in a
- * fixed 64 KiB device array of the library, looked up on the first call on
- * each device (make that first call outside any stream capture).  All calls
- * share that array, so calls that may overlap on the GPU race and must be
- * ordered by the caller.  Asynchronous; returns HD_ERR_ARG for NULL pointers
- * or N out of range, HD_ERR_CUDA if a launch or the lookup fails.
+ * fixed 256 KiB device array of the library, held on every device that loads
+ * the library until the process exits.  Its device address is looked up on
+ * every call (cudaGetSymbolAddress, which allocates nothing); the first call
+ * on a device may load the library's device code, so make it outside any
+ * stream capture.  All calls share that array, so calls that may overlap on
+ * the GPU race and must be ordered by the caller.  Asynchronous; returns
+ * HD_ERR_ARG for NULL or misaligned pointers or N out of range, HD_ERR_CUDA
+ * if a launch or the lookup fails.
  */
 hd_status hd_psi6_mean_noalloc(const double *psi_local_device, int64_t N, double *out_device, void *stream);
 

@@ -4,6 +4,7 @@
 // kernels of hd_sweep.cu and hd_measure.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -79,7 +80,7 @@ struct hd_ctx {
     double* fit = nullptr;
     double* fit_qr = nullptr;  // Householder factor of the fit's design matrix
     double2* psi_local = nullptr;
-    double2* psi_part = nullptr;
+    hd::ExactPair* psi_part = nullptr;  // [blocks_t32] exact block sums of psi_j
     double* psi_res = nullptr;
     double* xy = nullptr;
     uint16_t* rep_of_act = nullptr;   // replica of each active-cell-grid block
@@ -607,6 +608,14 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     // cell arrays are padded to a multiple of 16 cells, so that every slot
     // plane starts on a 16-byte boundary (bulk copies need one)
     ctx->Ctot = (cell_off + 15) & ~int64_t(15);
+    // Test hook for the bulk-copy pass's error path: with the environment
+    // variable HD_TEST_UNALIGNED_SLOT_STRIDE=1 at creation, the slot planes
+    // are 8 cells further apart, so every plane after the first starts off
+    // the 16-cell boundary.  The cp.async kernels do not need that boundary;
+    // the bulk-copy pass rejects its staging plan, issues no copy and reports
+    // HD_ERR_TIMEOUT.
+    if (const char* t = std::getenv("HD_TEST_UNALIGNED_SLOT_STRIDE"); t && t[0] == '1' && t[1] == '\0')
+        ctx->Ctot += 8;
     ctx->Ntot = id_off;
     if (ctx->Ctot * int64_t(cap) >= (int64_t(1) << 31)) {
         delete ctx;

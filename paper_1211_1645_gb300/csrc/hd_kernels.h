@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "hd_device.cuh"
+#include "hd_exact.cuh"
 
 namespace hd {
 
@@ -91,8 +92,10 @@ cudaError_t launch_hist(const LaunchCfg& c, const HistCfg& h, CellBufs cells, un
 size_t fit_factor_len(int K);
 cudaError_t launch_fit_factor(cudaStream_t s, int K, double* qr);
 cudaError_t launch_fit(const LaunchCfg& c, int K, const double* qr, const unsigned long long* hist, double* res);
-cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err);
-cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res);
+// Local psi_6 into local (nullable) and each block's exact sum into partial
+// [blocks_t32]; the reduction rounds each replica's total once and divides by N.
+cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, ExactPair* partial, int* err);
+cudaError_t launch_psi6_reduce(const LaunchCfg& c, const ExactPair* partial, double* res);
 // Append (beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6) of every replica to
 // series[len] and advance len (bounded by cap; a full series sets err bit 4).
 cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* psi, double* series,

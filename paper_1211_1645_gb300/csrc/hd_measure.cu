@@ -485,7 +485,7 @@ __host__ __device__ constexpr size_t psi6_stage_bytes(int rows) {
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256, FIX ? 4 : 1)
 k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
-       const int32_t* __restrict__ pid, double2* __restrict__ local, double2* __restrict__ partial,
+       const int32_t* __restrict__ pid, double2* __restrict__ local, ExactPair* __restrict__ partial,
        int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     pdl_begin();
@@ -515,7 +515,7 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
     __shared__ uint16_t s_list[256 * CAP];
     __shared__ int s_warp[8];
     const int D = tile_disk_list(s_n, kPsiSX, kPsiHalo, X0, Y0, m, s_list, s_warp);
-    double sr = 0.0, si = 0.0;
+    Exact192 sr = exact_zero(), si = exact_zero();  // exact sums of this thread's psi_j
     int rmax = (m - 1) / 2;
     if constexpr (FIX) {
         const int lim = int((int64_t(1) << 31) / rep.W) - 1;
@@ -623,68 +623,40 @@ k_psi6(const Rep* __restrict__ reps, int R, const uint8_t* __restrict__ cnt, con
                     const double c6 = __dsub_rn(__dmul_rn(c4, c2), __dmul_rn(s4, s2));
                     const double s6 = __dadd_rn(__dmul_rn(c4, s2), __dmul_rn(s4, c2));
                     const double r6 = __dmul_rn(__dmul_rn(r2, r2), r2);
-                    const double inv = __ddiv_rn(1.0, r6);  // one division for both parts
-                    dr_ = __dadd_rn(dr_, __dmul_rn(c6, inv));
-                    di = __dadd_rn(di, __dmul_rn(s6, inv));
+                    dr_ = __dadd_rn(dr_, __ddiv_rn(c6, r6));
+                    di = __dadd_rn(di, __ddiv_rn(s6, r6));
                 }
                 pre = __ddiv_rn(dr_, 6.0);
                 pim = __ddiv_rn(di, 6.0);
             }
             if (local) local[rep.id_off + idme] = make_double2(pre, pim);
-            sr += pre;
-            si += pim;
+            exact_add(sr, pre);
+            exact_add(si, pim);
         }
     }
-    // fixed-order block reduction of the per-thread sums
-    __shared__ double s_re[32], s_im[32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        sr += __shfl_down_sync(0xffffffffu, sr, off);
-        si += __shfl_down_sync(0xffffffffu, si, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_re[warp] = sr;
-        s_im[warp] = si;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tr = 0.0, ti = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
-            tr += s_re[w];
-            ti += s_im[w];
-        }
-        partial[blockIdx.x] = make_double2(tr, ti);
-    }
+    // block sum: exact, so its value does not depend on the order of the disks
+    const ExactPair t = exact_block_sum(sr, si);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// Sum the block partials of each replica in a fixed order; Psi_6 = sum / N.
+// Psi_6 of each replica: the exact sum of its block partials rounded once to
+// double, then divided by N (the oracle's order of operations).
 __global__ void k_psi6_reduce(const Rep* __restrict__ reps, int R, int blocks_total,
-                              const double2* __restrict__ partial, double* __restrict__ res) {
+                              const ExactPair* __restrict__ partial, double* __restrict__ res) {
     pdl_begin();
     const int r = blockIdx.x;
     const Rep& rep = reps[r];
     const int b0 = rep.blk_t32;
     const int b1 = (r + 1 < R) ? reps[r + 1].blk_t32 : blocks_total;
-    double sr = 0.0, si = 0.0;
+    Exact192 sr = exact_zero(), si = exact_zero();
     for (int b = b0 + int(threadIdx.x); b < b1; b += blockDim.x) {
-        sr += partial[b].x;
-        si += partial[b].y;
+        exact_merge(sr, partial[b].re);
+        exact_merge(si, partial[b].im);
     }
-    __shared__ double s_re[1024], s_im[1024];
-    s_re[threadIdx.x] = sr;
-    s_im[threadIdx.x] = si;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (int(threadIdx.x) < s) {
-            s_re[threadIdx.x] += s_re[threadIdx.x + s];
-            s_im[threadIdx.x] += s_im[threadIdx.x + s];
-        }
-        __syncthreads();
-    }
+    const ExactPair t = exact_block_sum(sr, si);
     if (threadIdx.x == 0) {
-        res[2 * r] = s_re[0] / double(rep.N);
-        res[2 * r + 1] = s_im[0] / double(rep.N);
+        res[2 * r] = __ddiv_rn(exact_round(t.re), double(rep.N));
+        res[2 * r + 1] = __ddiv_rn(exact_round(t.im), double(rep.N));
     }
 }
 
@@ -728,7 +700,7 @@ cudaError_t launch_fit(const LaunchCfg& c, int K, const double* qr, const unsign
 }
 
 template <bool FIX, int CAP>
-static cudaError_t psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
+static cudaError_t psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, ExactPair* partial, int* err) {
     const size_t smem = psi6_stage_bytes<FIX, CAP>(c.threads / 32);
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
@@ -740,7 +712,7 @@ static cudaError_t psi6_t(const LaunchCfg& c, CellBufs cells, double2* local, do
                     err);
 }
 
-cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, double2* partial, int* err) {
+cudaError_t launch_psi6(const LaunchCfg& c, CellBufs cells, double2* local, ExactPair* partial, int* err) {
     if (c.fixed) return c.cap == 4 ? psi6_t<true, 4>(c, cells, local, partial, err) : psi6_t<true, 9>(c, cells, local, partial, err);
     return c.cap == 4 ? psi6_t<false, 4>(c, cells, local, partial, err) : psi6_t<false, 9>(c, cells, local, partial, err);
 }
@@ -769,8 +741,8 @@ cudaError_t launch_record(const LaunchCfg& c, const double* fit, const double* p
     return launch_k(k_record, dim3(1), dim3(((c.R + 31) / 32) * 32), 0, c.stream, c.R, fit, psi, series, len, cap, err);
 }
 
-cudaError_t launch_psi6_reduce(const LaunchCfg& c, const double2* partial, double* res) {
-    return launch_k(k_psi6_reduce, dim3(c.R), dim3(256), 0, c.stream, c.reps, c.R, c.blocks_t32, partial, res);
+cudaError_t launch_psi6_reduce(const LaunchCfg& c, const ExactPair* partial, double* res) {
+    return launch_k(k_psi6_reduce, dim3(c.R), dim3(1024), 0, c.stream, c.reps, c.R, c.blocks_t32, partial, res);
 }
 
 }  // namespace hd

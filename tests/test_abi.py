@@ -113,3 +113,40 @@ def test_no_cpu_fallback_without_gpu(hdlib):
     with pytest.raises(b.HDError) as e:
         b.hd_init(256, 0.7, 1.0, 0.1, 1)
     assert e.value.status == b.HD_ERR_CUDA
+
+
+def comment_of_each_declaration():
+    """Map each declared hd_* call to the comment that documents it: the
+    nearest block comment before its declaration that starts a line (comments
+    trailing code on a line, such as field notes, are not documentation of a
+    call).  One block may document a group of calls declared under it."""
+    text = open(HEADER).read()
+    out = {}
+    last = ""
+    for m in re.finditer(r"(?m)^[ \t]*(/\*.*?\*/)|/\*.*?\*/|\b(hd_[a-z0-9_]+)\s*\(", text, flags=re.S):
+        if m.group(1):
+            last = m.group(1)
+        elif m.group(2):
+            out.setdefault(m.group(2), last)
+    return out
+
+
+def test_every_call_cites_its_passage():
+    """Each exported call's comment names the section, equation or table of
+    the paper that defines it, or states that the paper has no counterpart."""
+    cites = re.compile(r"Sec\.|Eqs?\.|Table|no counterpart")
+    docs = comment_of_each_declaration()
+    missing = [s for s in declared_symbols() if not cites.search(docs.get(s, ""))]
+    assert not missing, missing
+
+
+def test_noalloc_rejects_misaligned_pointers_on_host(hdlib):
+    """The allocation-free Psi_6 mean reads doubles: a pointer that is not
+    8-byte aligned is rejected before any device work (no GPU needed)."""
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    V = ctypes.c_void_p
+    assert lib.hd_psi6_mean_noalloc(V(0x10004), ctypes.c_int64(16), V(0x20000), None) == b.HD_ERR_ARG
+    assert lib.hd_psi6_mean_noalloc(V(0x10000), ctypes.c_int64(16), V(0x20004), None) == b.HD_ERR_ARG
+    assert lib.hd_psi6_mean_noalloc(None, ctypes.c_int64(16), V(0x20000), None) == b.HD_ERR_ARG
+    assert lib.hd_psi6_mean_noalloc(V(0x10000), ctypes.c_int64(0), V(0x20000), None) == b.HD_ERR_ARG
