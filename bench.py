@@ -16,10 +16,18 @@ Each step is one graph launch of the library (hd_run).
 Secondary keys of the same line (same step and timing): `sweeps_only` (the
 same S sweeps without the measurement), `fp64` (the plain FP64 chain),
 `replicas4` (four replicas of the headline system in one context), `scan31`
-(the 31-replica equation-of-state scan) and `autotuned` (the headline system
-at the cell side and block size the autotuner picks).  `roofline.ncu` holds
-the committed ncu figures (L2 and pipe utilisation, issue activity,
-occupancy) of the dominant kernel while its sources are unchanged.
+(the 31-replica equation-of-state scan), `autotuned` (the headline system
+at the cell side and block size the autotuner picks) and `config5` (N =
+2048^2 at eta = 0.720, a state larger than L2, 250 sweeps and a measurement
+with the local psi_j field per step).
+
+Roofline: after the timed steps two more steps replay as profiled graphs
+(a timing event around every kernel node); each kernel class is charged its
+share of those event times x the graph-timed ms_per_step, and the dominant
+class's time per launch gives its achieved rates against three roofs (HBM
+copy bandwidth, L2-resident copy bandwidth, warp-instruction issue).  The
+binding roof is picked from the committed ncu counters of that kernel, which
+`roofline.ncu` repeats while the kernel's sources are unchanged.
 
 --impl reference times the CPU oracle (one core) on a bounded sample of the
 same workload instead.
@@ -86,7 +94,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -160,10 +168,13 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # the GPU arm
 # ---------------------------------------------------------------------------
 def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
-              block_threads=128, sweep_kernel=None, measure=True):
+              block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None):
     """Device-resident timing of `steps` steps of one form; returns a dict.
     N and eta may be per-replica lists (one batched context); attempts are
-    summed over replicas."""
+    summed over replicas.  measure: 0 sweeps only, 1 pressure and Psi_6 per
+    step, 2 also the local psi_j field kept on the device.  Afterwards two
+    more steps are replayed as profiled graphs (a timing event before and
+    after every kernel node) for the per-kernel device times."""
     import numpy as np
     import torch
 
@@ -175,7 +186,7 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     eta = args.eta if eta is None else eta
     if np.ndim(N) == 0:
         sysg = hd.HardDisks(N, eta, args.delta, args.seed + rank, precision=form,
-                            sweep_kernel=sweep_kernel or args.sweep_kernel,
+                            sweep_kernel=sweep_kernel or args.sweep_kernel, lattice=lattice,
                             cell_min=cell_min or args.cell_min, block_threads=block_threads)
     else:
         R = len(N)
@@ -185,10 +196,10 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
                             cell_min=cell_min or args.cell_min, block_threads=block_threads)
     sysg.set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    S = args.sweeps_per_step
+    S = sweeps or args.sweeps_per_step
 
     # one step = one graph launch: S sweeps + pressure and Psi_6 recorded on the device
-    # (measure=False: the S sweeps alone)
+    # (measure=0: the S sweeps alone)
     sysg.series_reserve(warmup + steps + 8)
 
     def step():
@@ -219,9 +230,9 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     l1 = sysg.kernel_times()
     launches = sum(l1[k][1] - l0[k][1] for k in l1)
 
-    # instrumented pass: per-kernel device time on the same workload
+    # profiled replays: per-kernel device time inside the step graph
     sysg.profile(True)
-    for _ in range(2):
+    for _ in range(PROFILED_STEPS):
         flush.zero_()
         step()
     kt = sysg.kernel_times()
@@ -229,9 +240,30 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     geo = sysg.geometry()
     series = sysg.series()
     sysg.close()
-    return {"ms": ms, "attempts": attempts, "launches": launches, "clocks": clocks, "kernel_times": kt,
-            "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None,
+    return {"ms": ms, "steps": steps, "attempts": attempts, "launches": launches, "clocks": clocks,
+            "kernel_times": kt, "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None,
             "acceptance": acceptance}
+
+
+PROFILED_STEPS = 2
+
+
+def in_step_times(run, ms_per_step):
+    """Per-step device time (ms) and launches of each kernel class from the
+    profiled graph replays, and the factor that charges each class its share
+    of the graph-timed step: in-step time of a class = its share of the
+    summed event times x ms_per_step.  The event nodes add a launch latency
+    to every kernel and serialise kernels that overlap in the timed graph, so
+    the event times themselves are not in-step durations (their sum is
+    typically 1.5x ms_per_step); the shares agree with the ncu launch list.
+    Any gap between kernels of the timed step is charged to the kernels,
+    which can only lower an achieved rate derived from these times."""
+    kt = run["kernel_times"]
+    per = {k: v[0] / PROFILED_STEPS for k, v in kt.items() if v[1]}
+    n = {k: v[1] / PROFILED_STEPS for k, v in kt.items() if v[1]}
+    total = sum(per.values())
+    scale = ms_per_step / total if total > 0 else 1.0
+    return per, n, total, scale
 
 
 # The equation-of-state scan: replica r has N = SCAN_N[r mod 5], eta = 0.700 + 0.001 r.
@@ -355,7 +387,7 @@ KERNEL_SOURCES = {
     "rebuild": ["hd_sweep.cu", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h"],
     "draws": ["hd_sweep.cu", "hd_device.cuh", "hd_kernels.h"],
     "hist": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h"],
-    "psi6": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h"],
+    "psi6": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
 }
 
 
@@ -405,6 +437,106 @@ def recorded_traffic(kernel, workload):
     return int(d["bytes_per_launch"]) if d else None
 
 
+_L2_GBS = None
+
+
+def l2_copy_gbs():
+    """Copy bandwidth of data resident in L2, measured here: a 24 MB buffer
+    copied into another (48 MB in all, well inside the 129 MB L2) 200 times
+    after a warm-up, read + write bytes over the CUDA-event time.  The
+    denominator of the L2 roof."""
+    global _L2_GBS
+    if _L2_GBS is None:
+        import torch
+        n = 24 << 20
+        a = torch.ones(n, dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        for _ in range(20):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(200):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        _L2_GBS = 2 * n * 200 / (e0.elapsed_time(e1) / 1e3) / 1e9
+    return _L2_GBS
+
+
+def roofline(per, nl, scale, ms_step, N, m, form, clocks, workload):
+    """Roofline of the dominant kernel class of a step.
+
+    Its in-step time per launch t is the profiled in-graph time, scaled by
+    `scale` (in_step_times).  Three roofs:
+      hbm    algorithmic bytes per launch / t against the measured HBM copy
+             bandwidth (MEASURED_PEAKS.json);
+      l2     the same bytes / t against the L2-resident copy bandwidth
+             measured by l2_copy_gbs;
+      issue  warp instructions per launch (committed ncu counters) / t
+             against one warp instruction per cycle per scheduler:
+             SMs x 4 x the median SM clock sampled during the timed steps.
+    The binding roof ("bound") is the one the committed ncu counters of the
+    kernel show closest to saturation (DRAM %, L2 %, issue-active %); the
+    top-level achieved / peak / frac are that roof's."""
+    import torch
+    top = max(per, key=lambda k: per[k])
+    t_s = per[top] * scale / max(1.0, nl[top]) / 1e3
+    alg = algorithmic_bytes(top, N, m, form)
+    hbm_peak, peak_kind = peaks()
+    out = {"kernel": top, "launches_per_step": nl[top], "in_step_us": t_s * 1e6, "time_scale": scale,
+           "algorithmic_bytes_per_launch": alg, "peak_kind": peak_kind,
+           "traffic": recorded_traffic(top, workload), "ncu": recorded_counters(top, workload)}
+    hbm = l2 = issue = None
+    if alg and t_s > 0:
+        a = alg / t_s / 1e9
+        hbm = {"achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak, "peak_kind": peak_kind}
+        lp = l2_copy_gbs()
+        l2 = {"achieved": a, "peak": lp, "unit": "GB/s", "frac": a / lp, "peak_kind": "measured L2 copy"}
+    cnt = out["ncu"]
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if cnt and cnt.get("warp_instructions") and mhz and t_s > 0:
+        a = cnt["warp_instructions"] / t_s / 1e9
+        p = sms * 4 * mhz * 1e6 / 1e9
+        issue = {"achieved": a, "peak": p, "unit": "G warp-instructions/s", "frac": a / p,
+                 "peak_kind": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (sampled)"}
+    bound = "hbm"
+    if cnt:
+        cands = {"hbm": cnt.get("dram_pct", 0.0), "l2": cnt.get("l2_pct", 0.0), "alu": cnt.get("issue_active_pct", 0.0)}
+        bound = max(cands, key=cands.get)
+        if bound == "alu" and issue is None:
+            bound = "hbm"
+    prim = {"hbm": hbm, "l2": l2, "alu": issue}[bound] or hbm
+    out.update({"bound": bound, "achieved": prim and prim["achieved"], "peak": prim and prim["peak"],
+                "unit": prim and prim["unit"], "frac": prim and prim["frac"], "hbm": hbm, "l2": l2, "issue": issue})
+    return out
+
+
+def time_config5(args, rank, world, dev):
+    """The state larger than L2: N = 2048^2 at eta = 0.720 from the
+    shifted-row lattice, fixed point, one step = 250 sweeps + the pressure,
+    the global Psi_6 and the local psi_j field kept on the device; its own
+    roofline (HBM is the binding roof once the state exceeds L2)."""
+    N, eta, S = 2048 * 2048, 0.720, 250
+    steps = max(2, args.steps // 20)
+    import torch
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    r = time_form(args, "fixed", rank, world, steps, 2, sampler, N=N, eta=eta, lattice="triangular", sweeps=S,
+                  measure=2)
+    t, a = reduce_max_sum(world, r["ms"], float(r["attempts"]), dev)
+    ms_step = t / steps
+    per, nl, ksum, scale = in_step_times(r, ms_step)
+    geo = r["geometry"]
+    return {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": ms_step, "steps": steps, "warmup": 2,
+            "config": f"N={N}, eta={eta}, shifted-row start, fixed form, {S} sweeps + pressure, Psi_6 and the "
+                      "local psi_j field per step; L2 flushed before each step",
+            "cells_per_side": geo["m"], "kernel_ms_per_step": {k: v * scale for k, v in per.items()},
+            "kernel_event_ms_per_step": per,
+            "clocks": r["clocks"],
+            "roofline": roofline(per, nl, scale, ms_step, N, geo["m"], "fixed", r["clocks"], f"{N}_fixed")}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_setup(args)
@@ -422,9 +554,10 @@ def run_ours(args):
         r = time_form(args, "fp64", rank, world, max(1, args.steps // 2), 1)
         t64, a64 = reduce_max_sum(world, r["ms"], float(r["attempts"]), dev)
         fp64 = {"value": a64 / (t64 / 1e3), "ms_per_step": t64 / max(1, args.steps // 2),
-                "kernel_ms_per_step": {k: v[0] / 2 for k, v in r["kernel_times"].items() if v[1]}}
+                "kernel_ms_per_step": (lambda p, n, t, sc: {k: v * sc for k, v in p.items()})(
+                    *in_step_times(r, t64 / max(1, args.steps // 2)))}
     # the sweep loop alone (rebuild + four colour passes per sweep), same timing
-    so = time_form(args, args.form, rank, world, max(1, args.steps // 2), 2, measure=False)
+    so = time_form(args, args.form, rank, world, max(1, args.steps // 2), 2, measure=0)
     tso, aso = reduce_max_sum(world, so["ms"], float(so["attempts"]), dev)
     sweeps_only = {"value": aso / (tso / 1e3), "unit": UNIT, "ms_per_step": tso / max(1, args.steps // 2),
                    "config": f"{args.sweeps_per_step} sweeps per step, no measurement"}
@@ -432,16 +565,14 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2))
     extras = None if args.no_extras else time_extras(args, rank, world, dev)
+    c5 = None if args.no_extras else time_config5(args, rank, world, dev)
     if rank != 0:
         return
-    kt = main["kernel_times"]
     geo = main["geometry"]
-    top = max(kt, key=lambda k: kt[k][0])  # dominant kernel class by device time
-    top_ms, top_n = kt[top]
-    top_avg_s = top_ms / max(1, top_n) / 1e3
-    peak, peak_kind = peaks()
-    alg = algorithmic_bytes(top, args.N, geo["m"], args.form)
-    achieved = alg / top_avg_s / 1e9 if (alg and top_avg_s > 0) else None
+    ms_step = tmax / args.steps
+    per, nl, ksum, scale = in_step_times(main, ms_step)
+    assert abs(ksum * scale - ms_step) <= 1e-9 * ms_step  # the classes' in-step times fill the step exactly
+    roof = roofline(per, nl, scale, ms_step, args.N, geo["m"], args.form, main["clocks"], f"{args.N}_{args.form}")
     line = {
         "metric": METRIC,
         "value": value,
@@ -461,14 +592,11 @@ def run_ours(args):
                    "trials_per_cell": geo["trials_per_cell"], "cell_side": geo["w"],
                    "acceptance": main["acceptance"], "l2": "flushed before each timed step (256 MB write)",
                    "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": recorded_traffic(top, f"{args.N}_{args.form}"),
-                     "kernel": top, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": alg, "avg_launch_us": top_avg_s * 1e6,
-                     "ncu": recorded_counters(top, f"{args.N}_{args.form}")},
+        "roofline": roof,
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
-        "kernel_ms_per_step": {k: v[0] / 2 for k, v in kt.items() if v[1]},
+        "kernel_ms_per_step": {k: v * scale for k, v in per.items()},
+        "kernel_event_ms_per_step": per,
         "last_measurement": dict(zip(["betaP_over_rho", "g_contact", "psi6_re", "psi6_im"],
                                      main["last_measurement"] or [])),
         "sweeps_only": sweeps_only,
@@ -477,6 +605,8 @@ def run_ours(args):
     }
     if extras:
         line.update(extras)
+    if c5:
+        line["config5"] = c5
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle(args, args.form, args.cpu_seconds)
     print(json.dumps(line), flush=True)

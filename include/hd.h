@@ -216,13 +216,23 @@ int32_t hd_replicas(const hd_ctx *ctx);
  * one batch): `steps` steps, each `sweeps_per_step` sweeps (as hd_sweep) and,
  * when `measure` != 0, one measurement of every replica -- the contact
  * pressure of hd_pressure and the global Psi_6 of hd_psi6 -- appended on the
- * device to a series (no host synchronisation).  Each distinct step is
- * captured once as a CUDA graph and replayed (directly launched while
- * profiling is enabled).  Asynchronous on the context stream.  R <= 1024.
- * Errors: HD_ERR_ARG for negative counts or an empty step; HD_ERR_REACH as
- * hd_pressure when measuring.
+ * device to a series (no host synchronisation).  measure == 2 also keeps the
+ * local psi_j field of each measurement (Eq. 8) on the device, for
+ * hd_psi6_local_device.  Each distinct step is captured once as a CUDA graph
+ * and replayed; while profiling is enabled the graph carries a timing event
+ * before and after every kernel, and each replay is followed by a
+ * synchronisation that adds the kernels' times to hd_kernel_times.
+ * Asynchronous on the context stream (unless profiling).  R <= 1024.
+ * Errors: HD_ERR_ARG for negative counts, an empty step or measure outside
+ * 0..2; HD_ERR_REACH as hd_pressure when measuring.
  */
 hd_status hd_run(hd_ctx *ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure);
+
+/* The local psi_j field (Eq. 8) of the last measurement that kept it
+ * (hd_psi6 with a local output, or hd_run with measure == 2), copied into a
+ * caller-owned device buffer of 2 * sum N_r doubles, (Re, Im) by disk id.
+ * Asynchronous. */
+hd_status hd_psi6_local_device(hd_ctx *ctx, double *local_device);
 
 /* Capacity of the measurement series of hd_run (pressure, Sec. II.C.1, and
  * Psi_6, Sec. III) in steps [4096, allocated by the first measuring hd_run];

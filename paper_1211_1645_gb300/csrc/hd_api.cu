@@ -98,14 +98,25 @@ struct hd_ctx {
     size_t ev_used = 0;
     // graph-captured steps (hd_run): one executable graph per (sweeps per step,
     // measure, starting buffer parity), with its kernel tallies
+    // A graph captured while profiling holds an event-record node before and
+    // after every kernel node (events gev[ev0 + 2i], gev[ev0 + 2i + 1] around
+    // its i-th kernel, of class ev_cls[i]), so that each replay times every
+    // kernel inside the graph, free of host launch gaps.
     struct StepGraph {
         int sweeps;
         bool measure;
         int parity;
+        bool local;     // the measurement keeps the psi_6 field
+        bool profiled;
         cudaGraphExec_t exec;
         int64_t launches[HD_KERNEL_CLASSES];
+        size_t ev0;
+        std::vector<int> ev_cls;
     };
     std::vector<StepGraph> graphs;
+    std::vector<cudaEvent_t> gev;         // event pool of profiled graphs
+    size_t gev_used = 0;
+    StepGraph* prof_capture = nullptr;    // the profiled graph being captured
     cudaStream_t capture_stream = nullptr;
     double* series = nullptr;       // [cap][R][4]: beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6
     int64_t* series_len = nullptr;  // device counter of recorded steps
@@ -348,6 +359,7 @@ hd_status check_flags(hd_ctx* ctx) {
 void drop_graphs(hd_ctx* ctx) {
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
+    ctx->gev_used = 0;
 }
 
 void free_ctx(hd_ctx* ctx) {
@@ -364,6 +376,7 @@ void free_ctx(hd_ctx* ctx) {
         if (q) cudaFree(q);
     if (ctx->series_len) cudaFree(ctx->series_len);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->gev) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }
@@ -387,6 +400,18 @@ bool prof_flush(hd_ctx* ctx) {
 template <class F>
 cudaError_t launch(hd_ctx* ctx, int cls, F&& f, bool capturing = false) {
     ctx->launches[cls] += 1;
+    if (capturing && ctx->prof_capture) {  // event nodes around the kernel node
+        hd_ctx::StepGraph& g = *ctx->prof_capture;
+        const size_t i = g.ev0 + 2 * g.ev_cls.size();
+        if (i + 2 > ctx->gev.size()) return cudaErrorInvalidValue;  // pool sized before the capture
+        cudaError_t e = cudaEventRecordWithFlags(ctx->gev[i], ctx->capture_stream, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+        e = f();
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecordWithFlags(ctx->gev[i + 1], ctx->capture_stream, cudaEventRecordExternal);
+        g.ev_cls.push_back(cls);
+        return e;
+    }
     if (!ctx->profiling || capturing) return f();
     if (ctx->ev_used + 2 > ctx->ev.size() && !prof_flush(ctx)) return cudaErrorUnknown;
     cudaError_t e = cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream);
@@ -460,12 +485,12 @@ cudaError_t enqueue_psi6(hd_ctx* ctx, cudaStream_t s, bool local, bool capturing
 
 // One hd_run step: sweeps, then (optionally) a measurement appended to the
 // device series.
-cudaError_t enqueue_step(hd_ctx* ctx, cudaStream_t s, int sweeps, bool measure, bool capturing) {
+cudaError_t enqueue_step(hd_ctx* ctx, cudaStream_t s, int sweeps, bool measure, bool local, bool capturing) {
     cudaError_t e = enqueue_sweeps(ctx, s, sweeps, capturing);
     if (e != cudaSuccess || !measure) return e;
     e = enqueue_pressure(ctx, s, capturing);
     if (e != cudaSuccess) return e;
-    e = enqueue_psi6(ctx, s, false, capturing);
+    e = enqueue_psi6(ctx, s, local, capturing);
     if (e != cudaSuccess) return e;
     return hd::launch_record(ctx->cfg(s), ctx->fit, ctx->psi_res, ctx->series, ctx->series_len, ctx->series_cap,
                              ctx->err);
@@ -808,6 +833,14 @@ hd_status hd_psi6(hd_ctx* ctx, double* re, double* im, double* local) {
     return HD_OK;
 }
 
+hd_status hd_psi6_local_device(hd_ctx* ctx, double* local_device) {
+    if (!ctx || !local_device) return HD_ERR_ARG;
+    if (ctx->sticky != HD_OK) return HD_ERR_STATE;
+    HD_CK(ctx, cudaMemcpyAsync(local_device, ctx->psi_local, sizeof(double2) * size_t(ctx->Ntot),
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    return HD_OK;
+}
+
 hd_status hd_positions_device(hd_ctx* ctx, double* xy_device) {
     if (!ctx || !xy_device) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
@@ -909,7 +942,8 @@ hd_status hd_series_reserve(hd_ctx* ctx, int64_t steps) {
 }
 
 hd_status hd_run(hd_ctx* ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure) {
-    if (!ctx || steps < 0 || sweeps_per_step < 0 || (sweeps_per_step == 0 && !measure) || ctx->R > 1024)
+    if (!ctx || steps < 0 || sweeps_per_step < 0 || (sweeps_per_step == 0 && !measure) || ctx->R > 1024 ||
+        measure < 0 || measure > 2)
         return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     if (measure)
@@ -920,44 +954,72 @@ hd_status hd_run(hd_ctx* ctx, int64_t steps, int32_t sweeps_per_step, int32_t me
         if (s != HD_OK) return s;
     }
     const bool meas = measure != 0;
-    if (ctx->profiling) {  // direct launches, so that every kernel is timed
-        for (int64_t k = 0; k < steps; ++k) HD_CK(ctx, enqueue_step(ctx, ctx->stream, sweeps_per_step, meas, false));
-    } else {
-        if (!ctx->capture_stream) HD_CK(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
-        for (int64_t k = 0; k < steps; ++k) {
-            const int parity = ctx->cur;
-            hd_ctx::StepGraph* g = nullptr;
-            for (auto& x : ctx->graphs)
-                if (x.sweeps == sweeps_per_step && x.measure == meas && x.parity == parity) g = &x;
-            if (!g) {
-                hd_ctx::StepGraph ng;
-                ng.sweeps = sweeps_per_step;
-                ng.measure = meas;
-                ng.parity = parity;
-                int64_t before[HD_KERNEL_CLASSES];
-                std::memcpy(before, ctx->launches, sizeof(before));
-                cudaGraph_t graph = nullptr;
-                HD_CK(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-                const cudaError_t ce = enqueue_step(ctx, ctx->capture_stream, sweeps_per_step, meas, true);
-                const cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &graph);
-                ctx->cur = parity;  // capture only recorded the launches
-                for (int c = 0; c < HD_KERNEL_CLASSES; ++c) {
-                    ng.launches[c] = ctx->launches[c] - before[c];
-                    ctx->launches[c] = before[c];
+    const bool local = measure == 2;
+    const bool prof = ctx->profiling;
+    if (prof && !prof_flush(ctx)) return fail_cuda(ctx);
+    if (!ctx->capture_stream) HD_CK(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    for (int64_t k = 0; k < steps; ++k) {
+        const int parity = ctx->cur;
+        hd_ctx::StepGraph* g = nullptr;
+        for (auto& x : ctx->graphs)
+            if (x.sweeps == sweeps_per_step && x.measure == meas && x.parity == parity && x.profiled == prof &&
+                x.local == local)
+                g = &x;
+        if (!g) {
+            hd_ctx::StepGraph ng;
+            ng.sweeps = sweeps_per_step;
+            ng.measure = meas;
+            ng.local = local;
+            ng.parity = parity;
+            ng.profiled = prof;
+            ng.ev0 = ctx->gev_used;
+            if (prof) {  // two events per launch: draws, 5 per sweep, the measurement
+                const size_t bound = 2 * (size_t(sweeps_per_step) * 5 + size_t(sweeps_per_step) / hd::kMaxChunk + 16);
+                while (ctx->gev.size() < ng.ev0 + bound) {
+                    cudaEvent_t e;
+                    HD_CK(ctx, cudaEventCreate(&e));
+                    ctx->gev.push_back(e);
                 }
-                if (ce != cudaSuccess || ee != cudaSuccess) {
-                    if (graph) cudaGraphDestroy(graph);
-                    return fail_cuda(ctx);
-                }
-                const cudaError_t ie = cudaGraphInstantiate(&ng.exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ie != cudaSuccess) return fail_cuda(ctx);
-                ctx->graphs.push_back(ng);
-                g = &ctx->graphs.back();
+                ctx->prof_capture = &ng;
+                hd::g_no_pdl = true;
             }
-            HD_CK(ctx, cudaGraphLaunch(g->exec, ctx->stream));
-            for (int c = 0; c < HD_KERNEL_CLASSES; ++c) ctx->launches[c] += g->launches[c];
-            if (sweeps_per_step & 1) ctx->cur ^= 1;
+            int64_t before[HD_KERNEL_CLASSES];
+            std::memcpy(before, ctx->launches, sizeof(before));
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                ce = enqueue_step(ctx, ctx->capture_stream, sweeps_per_step, meas, local, true);
+                const cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &graph);
+                if (ce == cudaSuccess) ce = ee;
+            }
+            ctx->prof_capture = nullptr;
+            hd::g_no_pdl = false;
+            ctx->cur = parity;  // capture only recorded the launches
+            for (int c = 0; c < HD_KERNEL_CLASSES; ++c) {
+                ng.launches[c] = ctx->launches[c] - before[c];
+                ctx->launches[c] = before[c];
+            }
+            if (ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail_cuda(ctx);
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&ng.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return fail_cuda(ctx);
+            ctx->gev_used = ng.ev0 + 2 * ng.ev_cls.size();
+            ctx->graphs.push_back(std::move(ng));
+            g = &ctx->graphs.back();
+        }
+        HD_CK(ctx, cudaGraphLaunch(g->exec, ctx->stream));
+        for (int c = 0; c < HD_KERNEL_CLASSES; ++c) ctx->launches[c] += g->launches[c];
+        if (sweeps_per_step & 1) ctx->cur ^= 1;
+        if (prof) {  // read this replay's kernel times before the next one
+            HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+            for (size_t i = 0; i < g->ev_cls.size(); ++i) {
+                float ms = 0.f;
+                HD_CK(ctx, cudaEventElapsedTime(&ms, ctx->gev[g->ev0 + 2 * i], ctx->gev[g->ev0 + 2 * i + 1]));
+                ctx->kernel_ms[g->ev_cls[i]] += double(ms);
+            }
         }
     }
     for (auto& s : ctx->sweeps) s += steps * sweeps_per_step;

@@ -37,6 +37,11 @@ struct LaunchCfg {
     cudaStream_t stream;
 };
 
+// Set on a host thread while it captures a step graph with timing events
+// between the kernels: programmatic dependent launch is then left off, since
+// an event node separates every pair of kernels.
+inline thread_local bool g_no_pdl = false;
+
 // Launch `kernel` on stream s; on a created stream the launch opts into
 // programmatic dependent launch, so the kernel's blocks may be scheduled while
 // the previous kernel drains (every kernel starts with pdl_begin()).
@@ -51,7 +56,7 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = s != nullptr ? 1 : 0;
+    cfg.numAttrs = (s != nullptr && !g_no_pdl) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

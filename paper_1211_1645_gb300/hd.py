@@ -93,6 +93,7 @@ def load(path: str | None = None):
             "hd_psi6": (S, [P, P, P, P]),
             "hd_positions": (S, [P, P]),
             "hd_positions_device": (S, [P, P]),
+            "hd_psi6_local_device": (S, [P, P]),
             "hd_set_positions": (S, [P, P]),
             "hd_stats": (S, [P, P, P]),
             "hd_get_geometry": (S, [P, c.c_int32, c.POINTER(hd_geometry)]),
@@ -239,6 +240,10 @@ def hd_positions_device(h, dev_ptr: int):
     _check(load().hd_positions_device(h, ctypes.c_void_p(dev_ptr)), "hd_positions_device")
 
 
+def hd_psi6_local_device(h, dev_ptr: int):
+    _check(load().hd_psi6_local_device(h, ctypes.c_void_p(dev_ptr)), "hd_psi6_local_device")
+
+
 def hd_set_positions(h, xy):
     a = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
     if a.shape[0] != _ntot(h):
@@ -254,8 +259,8 @@ def hd_stats(h):
     return a, b
 
 
-def hd_run(h, steps: int, sweeps_per_step: int, measure: bool = True):
-    _check(load().hd_run(h, int(steps), int(sweeps_per_step), int(bool(measure))), "hd_run")
+def hd_run(h, steps: int, sweeps_per_step: int, measure: int = 1):
+    _check(load().hd_run(h, int(steps), int(sweeps_per_step), int(measure)), "hd_run")
 
 
 def hd_series_reserve(h, steps: int):
@@ -432,7 +437,12 @@ class HardDisks:
         hd_set_stream(self.h, stream_ptr)
 
     def run(self, steps, sweeps_per_step, measure=True):
-        hd_run(self.h, steps, sweeps_per_step, measure)
+        """measure: False/0 sweeps only; True/1 pressure and Psi_6 per step;
+        2 also keeps each measurement's local psi_j field on the device."""
+        hd_run(self.h, steps, sweeps_per_step, int(measure))
+
+    def psi6_local_device(self, dev_ptr):
+        hd_psi6_local_device(self.h, dev_ptr)
 
     def series(self):
         return hd_series(self.h)

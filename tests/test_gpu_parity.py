@@ -398,3 +398,32 @@ def test_tma_pass_block_sizes(hd, oracle_mod, form, threads):
             o.sweep(n)
             assert_same_state(g, o)
         g.close()
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_profiled_graph_and_kept_local_field(hd, oracle_mod, form):
+    """hd_run while profiling (a timing event around every kernel node of the
+    step graph) runs the same chain, and times every launch; measure == 2
+    keeps each measurement's psi_j field on the device, equal to the
+    oracle's."""
+    import torch
+    g, o = make_pair(hd, oracle_mod, form, 1000, 0.70, 0.1, 41)
+    g.profile(True)
+    g.run(2, 5, measure=2)
+    kt = g.kernel_times()
+    g.profile(False)
+    assert kt["pass"][1] == 2 * 5 * 4 and kt["rebuild"][1] == 2 * 5 and kt["psi6"][1] == 2
+    assert all(ms > 0 for ms, n in kt.values() if n)
+    o.sweep(10)
+    assert_same_state(g, o)
+    field = torch.empty(2 * 1000, dtype=torch.float64, device="cuda")
+    g.psi6_local_device(field.data_ptr())
+    torch.cuda.synchronize()
+    f = field.cpu().numpy().reshape(-1, 2)
+    rloc, rglob = o.psi6()
+    assert np.array_equal(f[:, 0] + 1j * f[:, 1], rloc)
+    ser = g.series()
+    assert complex(ser[-1, 0, 2], ser[-1, 0, 3]) == rglob
+    g.run(1, 5, measure=True)  # the unprofiled graph of the same step
+    o.sweep(5)
+    assert_same_state(g, o)
