@@ -222,7 +222,7 @@ k_hist_tile(const Rep* __restrict__ reps, int R, int K, const double* __restrict
                         if (s_id[q * nS + sc] <= idme) continue;
                     }
                     const P2<FIX> o = s_pos[q * nS + sc];
-                    E r2;
+                    E r2 = E(0);
                     if constexpr (FIX) {
                         // |offset| < (RR + 1) W <= 5 W < 2^31
                         const int32_t rx = (o.x + dcx * rep.W) - me.x;

@@ -45,22 +45,36 @@ def test_set_delta_matches_oracle(hd, oracle_mod, form):
 
 
 def test_fixed_vs_fp64_equation_of_state(hd):
-    """beta P / rho at eta = 0.716, N = 64^2, eight independent replicas per
-    form (one batch each): the two forms' means agree within 3 combined
-    standard errors."""
-    R, N, eta = 8, 4096, 0.716
+    """Eq. 4 pressure at eta = 0.716, N = 64^2, in both number forms (two
+    different Markov chains of the same ensemble): sixteen independent
+    replicas per form in one batch, 1.5 10^5 sweeps of equilibration from the
+    square lattice, then 2 10^5 sweeps with the contact pressure every 1000.
+    Errors are batch means over the independent replicas (the spread of the
+    replica means).  Equilibration check: in each form the two halves of the
+    production run agree within 3 standard errors.  The two forms' P* must
+    agree within 3 combined standard errors."""
+    R, N, eta = 16, 4096, 0.716
+    equil, prod, every = 150_000, 200_000, 1000
     res = {}
     for form, seed0 in (("fixed", 100), ("fp64", 200)):
         g = hd.HardDisks([N] * R, [eta] * R, [0.1] * R, [seed0 + r for r in range(R)], precision=form)
-        g.sweep(4000)
-        g.series_reserve(64)
-        g.run(40, 100, measure=True)
-        s = g.series()[:, :, 0]  # [step, replica]
-        means = s.mean(axis=0)
-        res[form] = (means.mean(), means.std(ddof=1) / np.sqrt(R))
+        g.run(equil // every, every, False)
+        g.series_reserve(prod // every + 8)
+        g.run(prod // every, every, True)
+        s = g.series()  # [step, replica, 4]
+        etas = np.array([g.geometry(r)["eta"] for r in range(R)])
+        pstar = s[:, :, 0] * 4.0 * etas / np.pi  # P* = beta P (2 sigma)^2
         g.close()
+        T = pstar.shape[0]
+        assert T == prod // every
+        halves = [pstar[: T // 2].mean(axis=0), pstar[T // 2:].mean(axis=0)]
+        h_se = [h.std(ddof=1) / np.sqrt(R) for h in halves]
+        assert abs(halves[0].mean() - halves[1].mean()) < 3.0 * np.hypot(*h_se), (form, halves)
+        means = pstar.mean(axis=0)
+        res[form] = (means.mean(), means.std(ddof=1) / np.sqrt(R))
     (mf, sf), (md, sd) = res["fixed"], res["fp64"]
-    assert 7.0 < mf < 16.0 and 7.0 < md < 16.0  # dense liquid, still relaxing from the lattice
+    print(f"P* at eta = 0.716, N = 64^2: fixed point {mf:.4f} +- {sf:.4f}, FP64 {md:.4f} +- {sd:.4f}, "
+          f"difference {(mf - md) / np.hypot(sf, sd):+.2f} combined SE")
     assert abs(mf - md) < 3.0 * np.hypot(sf, sd), res
 
 
