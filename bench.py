@@ -168,7 +168,7 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # the GPU arm
 # ---------------------------------------------------------------------------
 def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
-              block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None):
+              block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None, threads_per_cell=1):
     """Device-resident timing of `steps` steps of one form; returns a dict.
     N and eta may be per-replica lists (one batched context); attempts are
     summed over replicas.  measure: 0 sweeps only, 1 pressure and Psi_6 per
@@ -187,13 +187,15 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     if np.ndim(N) == 0:
         sysg = hd.HardDisks(N, eta, args.delta, args.seed + rank, precision=form,
                             sweep_kernel=sweep_kernel or args.sweep_kernel, lattice=lattice,
-                            cell_min=cell_min or args.cell_min, block_threads=block_threads)
+                            cell_min=cell_min or args.cell_min, block_threads=block_threads,
+                            threads_per_cell=threads_per_cell)
     else:
         R = len(N)
         seeds = [args.seed + rank * R + r for r in range(R)]
         sysg = hd.HardDisks(list(N), list(eta), [args.delta] * R, seeds, precision=form,
                             sweep_kernel=sweep_kernel or args.sweep_kernel,
-                            cell_min=cell_min or args.cell_min, block_threads=block_threads)
+                            cell_min=cell_min or args.cell_min, block_threads=block_threads,
+                            threads_per_cell=threads_per_cell)
     sysg.set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     S = sweeps or args.sweeps_per_step
@@ -276,7 +278,7 @@ def time_extras(args, rank, world, dev):
     equation-of-state scan, and the headline system at the cell side, sweep
     kernel and block size the autotuner picks (sweeps only, then re-timed
     with measurement and L2 flush)."""
-    from paper_1211_1645_gb300.tune import autotune
+    from paper_1211_1645_gb300.tune import autotune, autotune_replicas
     out = {}
     steps, warm = max(1, args.steps // 2), 2
     r4 = time_form(args, args.form, rank, world, steps, warm, N=[args.N] * 4, eta=[args.eta] * 4)
@@ -291,18 +293,33 @@ def time_extras(args, rank, world, dev):
     out["scan31"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
                      "config": f"31 replicas, N = {{128^2 .. 512^2}} round-robin ({sum(Ns)} disks), "
                                "eta = 0.700 + 0.001 r, one context"}
+    # the scan with a cell side per replica and the batch's launch shape chosen by the autotuner
+    choice, stable = autotune_replicas(Ns, etas, args.delta, args.seed + rank * R, precision=args.form,
+                                       cell_mins=(2.0, 2.2, 2.4), block_threads=(128, 256),
+                                       threads_per_cell=(1, 2, 4))
+    if choice:
+        ra = time_form(args, args.form, rank, world, steps, warm, N=Ns, eta=etas, cell_min=choice["cell_min"],
+                       block_threads=choice["block_threads"], threads_per_cell=choice["threads_per_cell"])
+        t, a = reduce_max_sum(world, ra["ms"], float(ra["attempts"]), dev)
+        out["scan31_autotuned"] = {
+            "value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
+            "vs_default": (a / (t / 1e3)) / out["scan31"]["value"],
+            "choice": {"cell_min_per_replica": choice["cell_min"], "block_threads": choice["block_threads"],
+                       "threads_per_cell": choice["threads_per_cell"]},
+            "candidates": stable}
     best, table = autotune(args.N, args.eta, args.delta, args.seed + rank, precision=args.form,
                            cell_mins=(2.0, 2.2, 2.4), kernels=("split",), block_threads=(128, 256),
-                           sweeps=args.sweeps_per_step, steps=2)
+                           threads_per_cell=(1, 2, 4), sweeps=args.sweeps_per_step, steps=2)
     if best:
         rt = time_form(args, args.form, rank, world, steps, warm, cell_min=best["cell_min"],
-                       block_threads=best["block_threads"], sweep_kernel=best["sweep_kernel"])
+                       block_threads=best["block_threads"], sweep_kernel=best["sweep_kernel"],
+                       threads_per_cell=best["threads_per_cell"])
         t, a = reduce_max_sum(world, rt["ms"], float(rt["attempts"]), dev)
         out["autotuned"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
                             "choice": {k: best[k] for k in ("cell_min", "sweep_kernel", "block_threads",
-                                                            "cells_per_side", "trials_per_cell")},
-                            "candidates": [{k: c[k] for k in ("cell_min", "block_threads", "trial_moves_per_s")}
-                                           for c in table]}
+                                                            "threads_per_cell", "cells_per_side", "trials_per_cell")},
+                            "candidates": [{k: c[k] for k in ("cell_min", "block_threads", "threads_per_cell",
+                                                              "trial_moves_per_s")} for c in table]}
     return out
 
 

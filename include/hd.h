@@ -75,6 +75,16 @@ typedef struct hd_opts {
                                 launch per sweep, tiles staged in shared memory.
                                 All give bit-identical chains.  A bulk-copy pass
                                 that cannot stage its segments sets HD_ERR_TIMEOUT. */
+    int32_t threads_per_cell; /* G threads per active cell in the split colour pass:
+                                1, 2, 4 or 8 [1].  The G lanes share the cell's
+                                draws and proposals and split the overlap tests
+                                against its eight neighbours, combined by a warp
+                                ballot; the chain is the same.  G > 1 needs
+                                HD_SWEEP_SPLIT and block_threads * G <= 512.    */
+    const double *cell_min_per_replica; /* [R] minimum cell side of each replica
+                                (>= 2 sigma), e.g. chosen per state point by an
+                                autotuner; NULL: cell_min for every replica [NULL].
+                                Read during hd_init / hd_batch_init only.       */
 } hd_opts;
 
 enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1, HD_SWEEP_TMA = 2 };

@@ -42,6 +42,7 @@ struct hd_ctx {
     int K = 50;
     int lattice = 0;
     int threads = 128;
+    int tpc = 1;            // threads per active cell of the split colour pass
     bool fused = false;
     bool pass_tma = false;  // colour pass with bulk-copy (TMA) staging
     // analysis scratch, grown on demand and freed with the context
@@ -138,6 +139,7 @@ struct hd_ctx {
         c.cap = cap;
         c.fixed = fixed;
         c.threads = threads;
+        c.tpc = tpc;
         c.ntc = 0;
         for (int k : {1, 2})
             if (std::all_of(reps.begin(), reps.end(), [k](const hd::Rep& r) { return r.nt == k; })) c.ntc = k;
@@ -192,12 +194,13 @@ void set_hist_f32_bounds(Rep& r, double e0, double eK) {
 
 // Geometry of one chain (Sec. II.A, II.B).  Lengths in units of sigma.
 hd_status plan_replica(int64_t N, double eta, double sigma, double delta, uint64_t seed, const hd_opts& o,
-                       Plan& pl) {
+                       double cell_min, Plan& pl) {
     if (N < 2 || N > (int64_t(1) << 31) - 1 || !(eta > 0.0) || !(sigma > 0.0) || !(delta >= 0.0))
         return HD_ERR_ARG;
     const bool fixed = o.precision == HD_FIXED32;
     const double L = std::sqrt(double(N) * kPi / eta);
-    const int m = 2 * int(std::floor(L / (2.0 * o.cell_min)));
+    if (!(cell_min >= 2.0)) return HD_ERR_ARG;
+    const int m = 2 * int(std::floor(L / (2.0 * cell_min)));
     if (m < 4) return HD_ERR_ARG;
     const double w = L / double(m);
     if (!(w < 8.0)) return HD_ERR_ARG;
@@ -511,6 +514,8 @@ void hd_default_opts(hd_opts* o) {
     o->cell_min = 2.0;
     o->block_threads = 128;
     o->sweep_kernel = HD_SWEEP_SPLIT;
+    o->threads_per_cell = 1;
+    o->cell_min_per_replica = nullptr;
 }
 
 const char* hd_status_string(hd_status s) {
@@ -542,6 +547,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         if (opts_in->cell_min > 0.0) o.cell_min = opts_in->cell_min;
         if (opts_in->block_threads > 0) o.block_threads = opts_in->block_threads;
         o.sweep_kernel = opts_in->sweep_kernel;
+        if (opts_in->threads_per_cell > 0) o.threads_per_cell = opts_in->threads_per_cell;
+        o.cell_min_per_replica = opts_in->cell_min_per_replica;
     }
     if (o.precision != HD_FP64 && o.precision != HD_FIXED32) return HD_ERR_ARG;
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
@@ -549,11 +556,17 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
     if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT && o.sweep_kernel != HD_SWEEP_TMA)
         return HD_ERR_ARG;
+    {
+        const int g = o.threads_per_cell;
+        if (g != 1 && g != 2 && g != 4 && g != 8) return HD_ERR_ARG;
+        if (g > 1 && (o.sweep_kernel != HD_SWEEP_SPLIT || o.block_threads * g > 512)) return HD_ERR_ARG;
+    }
 
     std::vector<Plan> plans(static_cast<size_t>(R));
     int cap = 4;
     for (int r = 0; r < R; ++r) {
-        const hd_status s = plan_replica(N[r], eta[r], sigma, delta[r], seed[r], o, plans[size_t(r)]);
+        const double cm = o.cell_min_per_replica ? o.cell_min_per_replica[r] : o.cell_min;
+        const hd_status s = plan_replica(N[r], eta[r], sigma, delta[r], seed[r], o, cm, plans[size_t(r)]);
         if (s != HD_OK) return s;
         cap = std::max(cap, plans[size_t(r)].cap);
     }
@@ -567,6 +580,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->K = o.hist_bins;
     ctx->lattice = o.lattice;
     ctx->threads = o.block_threads;
+    ctx->tpc = o.threads_per_cell;
     ctx->fused = o.sweep_kernel == HD_SWEEP_FUSED;
     ctx->pass_tma = o.sweep_kernel == HD_SWEEP_TMA;
     ctx->tile = hd::fused_tile(ctx->fixed, cap);

@@ -27,7 +27,8 @@ struct LaunchCfg {
     int R;
     int cap;           // 4 or 9
     bool fixed;        // fixed-point form
-    int threads;       // threads per block
+    int threads;       // threads per block (cells per block of the active-cell grid)
+    int tpc;           // threads per active cell of the split colour pass (1, 2, 4 or 8)
     int ntc;           // trials per occupied cell and pass when every replica has the same 1 or 2, else 0
     int blocks_cell;   // whole-cell grid size (all replicas)
     int blocks_act;    // active-cell grid size (all replicas)
@@ -65,6 +66,9 @@ cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBu
                            int* err);
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters);
+// The colour pass with tpc > 1 threads per active cell (blocks of threads x tpc).
+cudaError_t launch_pass_group(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
+                              unsigned long long* counters);
 // The colour pass with each block's neighbourhood staged by bulk copies (TMA).
 cudaError_t launch_pass_tma(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                             unsigned long long* counters, int* err);

@@ -454,6 +454,7 @@ static cudaError_t pass_nt(const LaunchCfg& c, const Frame* table, int j, int p,
 
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters) {
+    if (c.tpc > 1) return launch_pass_group(c, table, j, p, cells, counters);
     if (c.fixed) return c.cap == 4 ? pass_nt<true, 4>(c, table, j, p, cells, counters) : pass_nt<true, 9>(c, table, j, p, cells, counters);
     return c.cap == 4 ? pass_nt<false, 4>(c, table, j, p, cells, counters) : pass_nt<false, 9>(c, table, j, p, cells, counters);
 }

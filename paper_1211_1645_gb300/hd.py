@@ -38,6 +38,8 @@ class hd_opts(ctypes.Structure):
         ("cell_min", ctypes.c_double),
         ("block_threads", ctypes.c_int32),
         ("sweep_kernel", ctypes.c_int32),
+        ("threads_per_cell", ctypes.c_int32),
+        ("cell_min_per_replica", ctypes.c_void_p),
     ]
 
 
@@ -149,16 +151,26 @@ SWEEP_KERNELS = {"split": 0, "fused": 1, "tma": 2}
 
 
 def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=50, hist_dr=1e-3,
-              cell_min=2.0, block_threads=128, sweep_kernel="split") -> hd_opts:
+              cell_min=2.0, block_threads=128, sweep_kernel="split", threads_per_cell=1) -> hd_opts:
+    """hd_opts from keyword values.  cell_min may be one value or one per
+    replica (a sequence); the per-replica array is kept alive on the returned
+    struct until it is dropped (the library reads it only at creation)."""
     o = hd_default_opts()
     o.precision = PRECISIONS.get(precision, precision)
     o.lattice = LATTICES.get(lattice, lattice)
     o.trials_per_cell = int(trials_per_cell)
     o.hist_bins = int(hist_bins)
     o.hist_dr = float(hist_dr)
-    o.cell_min = float(cell_min)
+    if np.ndim(cell_min) == 0:
+        o.cell_min = float(cell_min)
+    else:
+        per = np.ascontiguousarray(cell_min, dtype=np.float64)
+        o.cell_min = float(per.min())
+        o._cell_min_keep = per
+        o.cell_min_per_replica = per.ctypes.data_as(ctypes.c_void_p)
     o.block_threads = int(block_threads)
     o.sweep_kernel = SWEEP_KERNELS.get(sweep_kernel, sweep_kernel)
+    o.threads_per_cell = int(threads_per_cell)
     return o
 
 
@@ -391,9 +403,10 @@ class HardDisks:
     """Convenience owner of one context (R >= 1 replicas)."""
 
     def __init__(self, N, eta, delta, seed, sigma=1.0, precision="fp64", lattice="square", trials_per_cell=0,
-                 hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128, sweep_kernel="split"):
+                 hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128, sweep_kernel="split",
+                 threads_per_cell=1):
         opts = make_opts(precision, lattice, trials_per_cell, hist_bins, hist_dr, cell_min, block_threads,
-                         sweep_kernel)
+                         sweep_kernel, threads_per_cell)
         if np.ndim(N) == 0:
             self.h = hd_init(N, eta, sigma, delta, seed, opts)
         else:

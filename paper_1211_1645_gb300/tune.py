@@ -1,28 +1,38 @@
 """Performance autotuner for the sweep.
 
-Chooses, for one workload, the minimum cell side (any side >= 2 sigma is a
-valid MPMC cell system, Sec. II.B; larger cells hold more disks and make
-more trials per cell), the sweep kernel (split launches or one fused
-shared-memory launch per sweep) and the threads per block of the split
-kernels, by timing graph-captured steps of the library on the current GPU.
+Any cell side of at least 2 sigma is a valid MPMC cell system (Sec. II.B):
+larger cells hold more disks and make more trials per occupied cell, smaller
+ones are cheaper per trial.  The autotuner chooses, by timing graph-captured
+steps of the library on the current GPU:
+
+* for one workload (``autotune``): the minimum cell side, the sweep kernel
+  (split launches or one fused shared-memory launch per sweep), the threads
+  per block of the split kernels and the threads per active cell of the
+  split colour pass (1, or a group of 2, 4 or 8 lanes that split the overlap
+  tests and combine them with a warp ballot);
+* for a batch of replicas at different state points, such as the
+  equation-of-state scan of Sec. IV.A (``autotune_replicas``): first each
+  replica's own cell side, timed on that replica alone, then the threads per
+  block and per cell of the whole batch with those cell sides.
+
 Every candidate runs the same chain definition, so only speed is compared;
 the trial count per step is read back from the library, so a candidate that
 makes cheaper (e.g. more often rejected) trials is not favoured unduly --
-only attempted trial moves per second count.
+only attempted trial moves per second count.  The step size delta is tuned
+separately, toward an acceptance target (hd_tune_delta), because it changes
+the chain's dynamics rather than its speed.
 """
 from __future__ import annotations
 
 import itertools
 
+import numpy as np
+
 from .hd import HardDisks
 
 
-def time_config(N, eta, delta, seed, precision, cell_min, sweep_kernel, block_threads, sweeps=50, steps=3):
-    """Attempted trial moves per second of `steps` graph-captured steps of
-    `sweeps` sweeps (after one untimed step), timed with CUDA events."""
+def _time(g, sweeps, steps):
     import torch
-    g = HardDisks(N, eta, delta, seed, precision=precision, cell_min=cell_min, sweep_kernel=sweep_kernel,
-                  block_threads=block_threads)
     stream = torch.cuda.current_stream()
     g.set_stream(stream.cuda_stream)
     g.run(1, sweeps, measure=False)
@@ -34,25 +44,79 @@ def time_config(N, eta, delta, seed, precision, cell_min, sweep_kernel, block_th
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    attempts = int(g.stats()[0].sum()) - a0
+    return (int(g.stats()[0].sum()) - a0) / (ms / 1e3)
+
+
+def time_config(N, eta, delta, seed, precision, cell_min, sweep_kernel, block_threads, sweeps=50, steps=3,
+                threads_per_cell=1):
+    """Attempted trial moves per second of `steps` graph-captured steps of
+    `sweeps` sweeps (after one untimed step), timed with CUDA events.  N, eta,
+    delta, seed and cell_min may be per-replica lists (one batched context)."""
+    g = HardDisks(N, eta, delta, seed, precision=precision, cell_min=cell_min, sweep_kernel=sweep_kernel,
+                  block_threads=block_threads, threads_per_cell=threads_per_cell)
+    rate = _time(g, sweeps, steps)
     geo = g.geometry()
     g.close()
     return {"cell_min": cell_min, "sweep_kernel": sweep_kernel, "block_threads": block_threads,
-            "cells_per_side": geo["m"], "trials_per_cell": geo["trials_per_cell"],
-            "trial_moves_per_s": attempts / (ms / 1e3)}
+            "threads_per_cell": threads_per_cell, "cells_per_side": geo["m"],
+            "trials_per_cell": geo["trials_per_cell"], "trial_moves_per_s": rate}
 
 
 def autotune(N, eta, delta, seed=1, precision="fixed", cell_mins=(2.0, 2.2, 2.4), kernels=("split", "fused"),
-             block_threads=(64, 128, 256), sweeps=50, steps=3):
+             block_threads=(64, 128, 256), threads_per_cell=(1,), sweeps=50, steps=3):
     """Time every candidate and return (best, all results sorted by speed).
-    Candidates whose geometry is invalid for the workload are skipped."""
+    Candidates whose geometry or launch shape is invalid for the workload are
+    skipped (the library rejects them at creation)."""
     results = []
-    for cm, kern, bt in itertools.product(cell_mins, kernels, block_threads):
-        if kern == "fused" and bt != block_threads[0]:
-            continue  # the fused kernel has a fixed block size
+    for cm, kern, bt, g in itertools.product(cell_mins, kernels, block_threads, threads_per_cell):
+        if kern == "fused" and (bt != block_threads[0] or g != 1):
+            continue  # the fused kernel has a fixed block size and one thread per cell
+        if kern == "tma" and g != 1:
+            continue
         try:
-            results.append(time_config(N, eta, delta, seed, precision, cm, kern, bt, sweeps, steps))
+            results.append(time_config(N, eta, delta, seed, precision, cm, kern, bt, sweeps, steps, g))
         except Exception:  # an invalid candidate (e.g. a cell too wide for the box)
             continue
     results.sort(key=lambda r: -r["trial_moves_per_s"])
     return (results[0] if results else None), results
+
+
+def autotune_replicas(Ns, etas, delta, seed=1, precision="fixed", cell_mins=(2.0, 2.2, 2.4),
+                      block_threads=(128, 256), threads_per_cell=(1, 2), sweeps=20, steps=2):
+    """Per-replica cell sides for a batch, then the batch's launch shape.
+
+    Stage 1: for each distinct state point (N, eta) of the batch, every cell
+    side in `cell_mins` is timed on a single-replica context (split kernel,
+    128 threads); the fastest is that replica's cell side.  Stage 2: the whole
+    batch, with those cell sides, is timed for every (block_threads,
+    threads_per_cell) candidate.  Returns (choice, table) where choice holds
+    the per-replica "cell_min" list, "block_threads", "threads_per_cell" and
+    the batch's "trial_moves_per_s", and table the stage-2 results."""
+    R = len(Ns)
+    deltas = list(delta) if np.ndim(delta) else [float(delta)] * R
+    per_point = {}
+    for n, e in sorted(set(zip(Ns, etas))):
+        best, best_rate = None, -1.0
+        for cm in cell_mins:
+            try:
+                r = time_config(n, e, deltas[0], seed, precision, cm, "split", 128, sweeps, steps)
+            except Exception:
+                continue
+            if r["trial_moves_per_s"] > best_rate:
+                best, best_rate = cm, r["trial_moves_per_s"]
+        per_point[(n, e)] = best if best is not None else 2.0
+    cms = [per_point[(n, e)] for n, e in zip(Ns, etas)]
+    seeds = [seed + r for r in range(R)]
+    table = []
+    for bt, g in itertools.product(block_threads, threads_per_cell):
+        try:
+            t = time_config(list(Ns), list(etas), deltas, seeds, precision, cms, "split", bt, sweeps, steps, g)
+        except Exception:
+            continue
+        table.append({"block_threads": bt, "threads_per_cell": g, "trial_moves_per_s": t["trial_moves_per_s"]})
+    table.sort(key=lambda r: -r["trial_moves_per_s"])
+    if not table:
+        return None, table
+    choice = dict(table[0])
+    choice["cell_min"] = cms
+    return choice, table

@@ -62,6 +62,10 @@ def test_status_strings_and_defaults(hdlib):
     (256, 0.7, 1.0, 0.1, {"hist_bins": 10000}),   # too many bins for the fit
     (256, 0.7, 1.0, 0.1, {"hist_bins": 4}),       # too few bins for a quartic
     (256, 0.7, 1.0, 0.1, {"block_threads": 100}),  # not a warp multiple
+    (256, 0.7, 1.0, 0.1, {"threads_per_cell": 3}),  # not 1, 2, 4 or 8 lanes
+    (256, 0.7, 1.0, 0.1, {"threads_per_cell": 8}),  # 128 cells x 8 lanes > 512 threads
+    (256, 0.7, 1.0, 0.1, {"threads_per_cell": 2, "sweep_kernel": "tma"}),  # groups only in the split pass
+    (256, 0.7, 1.0, 0.1, {"cell_min": [1.9]}),     # a per-replica cell side below a diameter
 ])
 def test_invalid_arguments_rejected_on_host(hdlib, N, eta, sigma, delta, kw):
     hd, lib = hdlib

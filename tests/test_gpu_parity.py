@@ -39,8 +39,14 @@ def hd():
 
 def make_pair(hd, oracle_mod, form, N, eta, delta, seed, lattice="square", nt=0, cell_min=2.0, K=50, dr=1e-3,
               kernel="split"):
+    """kernel: "split", "tma", "fused", or "split-g<G>" for the split pass with
+    G threads per active cell."""
+    tpc = 1
+    if kernel.startswith("split-g"):
+        kernel, tpc = "split", int(kernel[len("split-g"):])
     g = hd.HardDisks(N, eta, delta, seed, precision=form, lattice=lattice, trials_per_cell=nt, cell_min=cell_min,
-                     hist_bins=K, hist_dr=dr, sweep_kernel=kernel)
+                     hist_bins=K, hist_dr=dr, sweep_kernel=kernel, threads_per_cell=tpc,
+                     block_threads=64 if tpc == 8 else 128)
     o = oracle_mod.OracleChain(N, eta, delta, seed, form=form, lattice=lattice, nt=nt, cell_min=cell_min)
     return g, o
 
@@ -51,12 +57,14 @@ def assert_same_state(g, o):
     assert np.array_equal(g.positions(), o.positions())
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma", "split-g2", "split-g4", "split-g8"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
-    """Both sweep kernels: one launch per sweep with shared-memory tiles, and
-    a rebuild launch plus four colour-pass launches."""
+    """Every sweep kernel: one launch per sweep with shared-memory tiles; a
+    rebuild launch plus four colour-pass launches (one thread per active
+    cell, bulk-copy staging, or G = 2, 4, 8 threads per cell with a warp
+    ballot over the overlap tests)."""
     g, o = make_pair(hd, oracle_mod, form, kernel=kernel, **CASES[case])
     geo, ogeo = g.geometry(), o.geometry()
     assert geo["m"] == ogeo["m"] and geo["L"] == ogeo["L"] and geo["trials_per_cell"] == ogeo["nt"]
@@ -427,3 +435,36 @@ def test_profiled_graph_and_kept_local_field(hd, oracle_mod, form):
     g.run(1, 5, measure=True)  # the unprofiled graph of the same step
     o.sweep(5)
     assert_same_state(g, o)
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_batched_replicas_per_replica_cell_sides(hd, oracle_mod, form):
+    """Replicas with their own minimum cell sides (as the autotuner picks them
+    per state point) in one context: each equals its own oracle chain with
+    that cell side (trials per occupied cell 1, 2, 2 and 3, capacity-9
+    cells), also with two threads per active cell."""
+    Ns = [24 ** 2, 20 ** 2, 32 ** 2, 17 ** 2]
+    etas = [0.70, 0.71, 0.705, 0.60]
+    cms = [2.0, 2.4, 2.2, 3.0]
+    seeds = [61, 62, 63, 64]
+    for tpc in (1, 2):
+        g = hd.HardDisks(Ns, etas, [0.1] * 4, seeds, precision=form, cell_min=cms, threads_per_cell=tpc)
+        os_ = [oracle_mod.OracleChain(n, e, 0.1, sd, form=form, cell_min=cm) for n, e, sd, cm in zip(Ns, etas, seeds, cms)]
+        for r, o in enumerate(os_):
+            geo = g.geometry(r)
+            assert geo["m"] == o.geometry()["m"] and geo["w"] >= cms[r]
+        assert g.geometry(0)["w"] < 2.4 and g.geometry(3)["trials_per_cell"] == 3
+        g.run(3, 10, measure=True)
+        for o in os_:
+            o.sweep(30)
+        att, acc = g.stats()
+        xy = g.positions()
+        ser = g.series()
+        off = 0
+        for r, o in enumerate(os_):
+            assert (int(att[r]), int(acc[r])) == o.stats()
+            assert np.array_equal(xy[off:off + Ns[r]], o.positions())
+            _, rglob = o.psi6()
+            assert complex(ser[-1, r, 2], ser[-1, r, 3]) == rglob
+            off += Ns[r]
+        g.close()

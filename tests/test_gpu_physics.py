@@ -80,10 +80,35 @@ def test_fixed_vs_fp64_equation_of_state(hd):
 
 def test_autotuner_picks_a_valid_fast_configuration(hd):
     from paper_1211_1645_gb300.tune import autotune
-    best, table = autotune(65536, 0.708, 0.1, cell_mins=(2.0, 2.4), block_threads=(128, 256), sweeps=20, steps=2)
-    assert best is not None and len(table) >= 3
+    best, table = autotune(65536, 0.708, 0.1, cell_mins=(2.0, 2.4), block_threads=(128, 256),
+                           threads_per_cell=(1, 2), sweeps=20, steps=2)
+    assert best is not None and len(table) >= 6
     assert best["trial_moves_per_s"] == max(r["trial_moves_per_s"] for r in table)
     assert best["cell_min"] in (2.0, 2.4) and best["sweep_kernel"] in ("split", "fused")
+    assert {r["threads_per_cell"] for r in table} == {1, 2}
+
+
+def test_autotuner_per_replica_choice_runs_the_same_chains(hd, oracle_mod):
+    """autotune_replicas picks a cell side per state point and the batch's
+    launch shape; a batch built from its choice runs each replica's own chain
+    (as the oracle with that cell side)."""
+    from paper_1211_1645_gb300.tune import autotune_replicas
+    Ns, etas = [32 ** 2, 24 ** 2, 32 ** 2], [0.70, 0.60, 0.72]
+    choice, table = autotune_replicas(Ns, etas, 0.1, seed=5, cell_mins=(2.0, 2.6), block_threads=(64, 128),
+                                      threads_per_cell=(1, 2), sweeps=10, steps=2)
+    assert choice is not None and len(choice["cell_min"]) == 3 and len(table) == 4
+    assert choice["trial_moves_per_s"] == max(r["trial_moves_per_s"] for r in table)
+    g = hd.HardDisks(Ns, etas, [0.1] * 3, [5, 6, 7], precision="fixed", cell_min=choice["cell_min"],
+                     block_threads=choice["block_threads"], threads_per_cell=choice["threads_per_cell"])
+    g.run(2, 10, False)
+    xy = g.positions()
+    off = 0
+    for r, (n, e, cm) in enumerate(zip(Ns, etas, choice["cell_min"])):
+        o = oracle_mod.OracleChain(n, e, 0.1, 5 + r, form="fixed", cell_min=cm)
+        o.sweep(20)
+        assert np.array_equal(xy[off:off + n], o.positions())
+        off += n
+    g.close()
 
 
 @pytest.mark.slow
