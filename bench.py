@@ -308,7 +308,7 @@ def time_extras(args, rank, world, dev):
                        "threads_per_cell": choice["threads_per_cell"]},
             "candidates": stable}
     best, table = autotune(args.N, args.eta, args.delta, args.seed + rank, precision=args.form,
-                           cell_mins=(2.0, 2.2, 2.4), kernels=("split",), block_threads=(128, 256),
+                           cell_mins=(2.0, 2.2, 2.4), kernels=("split", "persistent"), block_threads=(128, 256),
                            threads_per_cell=(1, 2, 4), sweeps=args.sweeps_per_step, steps=2)
     if best:
         rt = time_form(args, args.form, rank, world, steps, warm, cell_min=best["cell_min"],
@@ -318,8 +318,9 @@ def time_extras(args, rank, world, dev):
         out["autotuned"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
                             "choice": {k: best[k] for k in ("cell_min", "sweep_kernel", "block_threads",
                                                             "threads_per_cell", "cells_per_side", "trials_per_cell")},
-                            "candidates": [{k: c[k] for k in ("cell_min", "block_threads", "threads_per_cell",
-                                                              "trial_moves_per_s")} for c in table]}
+                            "candidates": [{k: c[k] for k in ("cell_min", "sweep_kernel", "block_threads",
+                                                              "threads_per_cell", "trial_moves_per_s")}
+                                           for c in table]}
     return out
 
 

@@ -72,9 +72,17 @@ typedef struct hd_opts {
                                 the same launches, each pass block staging its
                                 neighbourhood (six row segments of the colour
                                 planes) with bulk copies (TMA); HD_SWEEP_FUSED: one
-                                launch per sweep, tiles staged in shared memory.
-                                All give bit-identical chains.  A bulk-copy pass
-                                that cannot stage its segments sets HD_ERR_TIMEOUT. */
+                                launch per sweep, tiles staged in shared memory;
+                                HD_SWEEP_PERSISTENT: one launch for up to 256
+                                sweeps, its blocks taking rebuild and colour-pass
+                                work items of two-cell-row bands in order, each
+                                item starting once the previous phase is done in
+                                its band and the two next to it (a wavefront, no
+                                launch boundary between phases).  All give
+                                bit-identical chains.  A bulk-copy pass that
+                                cannot stage its segments, or a persistent sweep
+                                whose bounded dependency wait gives up, sets
+                                HD_ERR_TIMEOUT. */
     int32_t threads_per_cell; /* G threads per active cell in the split colour pass:
                                 1, 2, 4 or 8 [1].  The G lanes share the cell's
                                 draws and proposals and split the overlap tests
@@ -87,7 +95,7 @@ typedef struct hd_opts {
                                 Read during hd_init / hd_batch_init only.       */
 } hd_opts;
 
-enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1, HD_SWEEP_TMA = 2 };
+enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1, HD_SWEEP_TMA = 2, HD_SWEEP_PERSISTENT = 3 };
 
 /* Geometry of one replica as realised by the library. */
 typedef struct hd_geometry {
@@ -420,7 +428,7 @@ typedef enum hd_kernel_class {
     HD_K_PSI6 = 5,       /* local psi_6                                       */
     HD_K_PSI6_REDUCE = 6,/* global Psi_6 reduction                            */
     HD_K_POSITIONS = 7,  /* cell frame to global positions                    */
-    HD_K_SWEEP = 8,      /* one fused sweep (rebuild and four passes)         */
+    HD_K_SWEEP = 8,      /* whole sweeps in one launch (fused or persistent)  */
     HD_K_ANALYSIS = 9,   /* Psi_6 autocorrelation, correlation time, field    */
     HD_KERNEL_CLASSES = 10
 } hd_kernel_class;

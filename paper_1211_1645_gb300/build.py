@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhd.so")
 
-SOURCES = ["hd_sweep.cu", "hd_pass_group.cu", "hd_pass_tma.cu", "hd_fused.cu", "hd_measure.cu", "hd_analysis.cu", "hd_bin.cu", "hd_api.cu", "hd_noalloc.cu"]
+SOURCES = ["hd_sweep.cu", "hd_pass_group.cu", "hd_persist.cu", "hd_pass_tma.cu", "hd_fused.cu", "hd_measure.cu", "hd_analysis.cu", "hd_bin.cu", "hd_api.cu", "hd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 # -fmad=false / -ffp-contract=off: every FP64 and FP32 expression of the

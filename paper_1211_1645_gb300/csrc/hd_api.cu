@@ -45,6 +45,11 @@ struct hd_ctx {
     int tpc = 1;            // threads per active cell of the split colour pass
     bool fused = false;
     bool pass_tma = false;  // colour pass with bulk-copy (TMA) staging
+    bool persist = false;   // many sweeps per launch (wavefront over bands)
+    int bands = 0;          // bands of two cell rows over all replicas
+    uint32_t* persist_sync = nullptr;  // ticket, abort word and per-band progress of the persistent sweep
+    int persist_blocks = 0;            // its grid: the blocks resident at once
+    bool persist_stall = false;        // test hook (HD_TEST_PERSIST_STALL=1 at creation)
     // analysis scratch, grown on demand and freed with the context
     double2* acf = nullptr;     // [R][max_lag + 1]
     size_t acf_cap = 0;
@@ -140,6 +145,8 @@ struct hd_ctx {
         c.fixed = fixed;
         c.threads = threads;
         c.tpc = tpc;
+        c.persist_blocks = persist_blocks;
+        c.persist_stall = persist_stall;
         c.ntc = 0;
         for (int k : {1, 2})
             if (std::all_of(reps.begin(), reps.end(), [k](const hd::Rep& r) { return r.nt == k; })) c.ntc = k;
@@ -347,7 +354,7 @@ hd_status check_flags(hd_ctx* ctx) {
         ctx->sticky = HD_ERR_OVERFLOW;
         return HD_ERR_OVERFLOW;
     }
-    if (flag & 8) {  // a staging copy of the bulk-copy pass was refused or did not complete in time
+    if (flag & (8 | 16)) {  // a bulk-copy staging or a persistent sweep's dependency wait gave up
         ctx->sticky = HD_ERR_TIMEOUT;
         return HD_ERR_TIMEOUT;
     }
@@ -438,6 +445,14 @@ cudaError_t enqueue_sweeps(hd_ctx* ctx, cudaStream_t s, int64_t n, bool capturin
         e = launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); },
                    capturing);
         for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
+            if (ctx->persist) {  // the chunk's sweeps in one launch
+                e = launch(ctx, HD_K_SWEEP, [&] {
+                    return hd::launch_sweeps_persist(c, ctx->table, nc, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1],
+                                                     ctx->counters, ctx->err, ctx->persist_sync, ctx->bands);
+                }, capturing);
+                if (nc & 1) ctx->cur ^= 1;
+                break;
+            }
             if (ctx->fused) {
                 e = launch(ctx, HD_K_SWEEP, [&] {
                     return hd::launch_sweep_fused(c, ctx->table, j, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1],
@@ -554,7 +569,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
     if (!(o.cell_min >= 2.0) || o.hist_bins < 5 || o.hist_bins > kMaxBins || o.trials_per_cell < 0) return HD_ERR_ARG;
     if (o.block_threads < 32 || o.block_threads > 256 || (o.block_threads & 31)) return HD_ERR_ARG;
-    if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT && o.sweep_kernel != HD_SWEEP_TMA)
+    if (o.sweep_kernel != HD_SWEEP_FUSED && o.sweep_kernel != HD_SWEEP_SPLIT && o.sweep_kernel != HD_SWEEP_TMA &&
+        o.sweep_kernel != HD_SWEEP_PERSISTENT)
         return HD_ERR_ARG;
     {
         const int g = o.threads_per_cell;
@@ -583,6 +599,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ctx->tpc = o.threads_per_cell;
     ctx->fused = o.sweep_kernel == HD_SWEEP_FUSED;
     ctx->pass_tma = o.sweep_kernel == HD_SWEEP_TMA;
+    ctx->persist = o.sweep_kernel == HD_SWEEP_PERSISTENT;
     ctx->tile = hd::fused_tile(ctx->fixed, cap);
     ctx->sigma = sigma;
     ctx->sweeps.assign(size_t(R), 0);
@@ -592,7 +609,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         return HD_ERR_ARG;
     }
     int64_t cell_off = 0, id_off = 0;
-    int blk_cell = 0, blk_act = 0, blk_tile = 0, blk_t32 = 0, blk_seg = 0;
+    int blk_cell = 0, blk_act = 0, blk_tile = 0, blk_t32 = 0, blk_seg = 0, band0 = 0;
     for (int r = 0; r < R; ++r) {
         Rep rep = plans[size_t(r)].rep;
         rep.cell_off = cell_off;
@@ -616,7 +633,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         rep.segw = (rep.hm + rep.nseg - 1) / rep.nseg;
         rep.seg_mul = 0;
         rep.seg_sh = 0;
-        rep.pad_seg = 0;
+        rep.band0 = band0;
+        band0 += rep.hm;
         if (rep.nseg > 1) {  // invariant divisor nseg >= 2: see div_by
             int l = 0;
             while ((int64_t(1) << l) < rep.nseg) ++l;
@@ -706,6 +724,17 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ok = ok && dev_alloc(ctx, &ctx->rep_of_act, size_t(ctx->blocks_act));
     ok = ok && dev_alloc(ctx, &ctx->rep_of_cell, size_t(ctx->blocks_cell));
     ok = ok && dev_alloc(ctx, &ctx->xy, size_t(2 * ctx->Ntot));
+    ctx->bands = band0;
+    if (ctx->persist) {
+        // Test hook for the persistent sweep's bounded waits: with the
+        // environment variable HD_TEST_PERSIST_STALL=1 at creation, the first
+        // item of band 0 is never published and the waits give up after 4096
+        // polls, so the sweep reports HD_ERR_TIMEOUT.
+        if (const char* t = std::getenv("HD_TEST_PERSIST_STALL"); t && t[0] == '1' && t[1] == '\0')
+            ctx->persist_stall = true;
+        ok = ok && dev_alloc(ctx, &ctx->persist_sync, hd::persist_sync_words(ctx->bands));
+        ok = ok && hd::persist_grid(ctx->cfg(), &ctx->persist_blocks) == cudaSuccess && ctx->persist_blocks > 0;
+    }
     if (!ok) {
         free_ctx(ctx);
         return HD_ERR_CUDA;

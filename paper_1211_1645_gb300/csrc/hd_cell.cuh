@@ -21,6 +21,17 @@ using P2 = std::conditional_t<FIX, int2, double2>;
 // disk at liquid densities); higher slots only when the cell is that full.
 constexpr int kEagerSlots = 2;
 
+// Loads of cell data.  COH = false: through the read-only data path, valid
+// while no block of the launch writes the cells it reads (one launch per
+// rebuild and per colour pass).  COH = true: coherent loads cached in L2 only
+// (ld.global.cg), for a launch whose blocks read cells that other blocks
+// wrote earlier in the same launch, ordered by acquire / release flags.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_cell(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // One cell as loaded by a thread: occupancy and the first kEagerSlots slots
 // in registers; a higher slot is fetched when a (rare) crowded cell needs it.
 template <bool FIX, bool IDS>
@@ -30,16 +41,18 @@ struct CellRegs {
     int32_t id[IDS ? kEagerSlots : 1];
     int n;
 
+    template <bool COH = false>
     __device__ __forceinline__ P2<FIX> slot(int k, const P2<FIX>* __restrict__ pos, uint32_t stride) const {
         if (k == 0) return s[0];
         if (k == 1) return s[1];
-        return __ldg(pos + size_t(k) * stride + c);
+        return ld_cell<COH>(pos + size_t(k) * stride + c);
     }
+    template <bool COH = false>
     __device__ __forceinline__ int32_t slot_id(int k, const int32_t* __restrict__ pid, uint32_t stride) const {
         if constexpr (IDS) {
             if (k == 0) return id[0];
             if (k == 1) return id[1];
-            return __ldg(pid + size_t(k) * stride + c);
+            return ld_cell<COH>(pid + size_t(k) * stride + c);
         }
         return 0;
     }
@@ -47,22 +60,22 @@ struct CellRegs {
 
 // Occupancy of a cell, clamped to its capacity (a count above capacity only
 // arises after an overflow, which the kernels report through the error flag).
-template <int CAP>
+template <int CAP, bool COH = false>
 __device__ __forceinline__ int occupancy(const uint8_t* __restrict__ cnt, uint32_t c) {
-    const int n = __ldg(cnt + c);
+    const int n = ld_cell<COH>(cnt + c);
     return n < CAP ? n : CAP;
 }
 
-template <bool FIX, bool IDS, int CAP = 4>
+template <bool FIX, bool IDS, int CAP = 4, bool COH = false>
 __device__ __forceinline__ void load_cell(const uint8_t* __restrict__ cnt, const P2<FIX>* __restrict__ pos,
                                           const int32_t* __restrict__ pid, uint32_t stride, uint32_t c,
                                           CellRegs<FIX, IDS>& out) {
-    out.n = occupancy<CAP>(cnt, c);
+    out.n = occupancy<CAP, COH>(cnt, c);
     out.c = c;
 #pragma unroll
     for (int k = 0; k < kEagerSlots; ++k) {
-        out.s[k] = __ldg(pos + size_t(k) * stride + c);
-        if constexpr (IDS) out.id[k] = __ldg(pid + size_t(k) * stride + c);
+        out.s[k] = ld_cell<COH>(pos + size_t(k) * stride + c);
+        if constexpr (IDS) out.id[k] = ld_cell<COH>(pid + size_t(k) * stride + c);
     }
 }
 

@@ -44,7 +44,7 @@ struct Rep {
     int32_t segw;       // half-columns per segment, ceil((m/2) / nseg)
     uint32_t seg_mul;   // seg_mul, seg_sh: divide by nseg >= 2 with div_by
     int32_t seg_sh;
-    int32_t pad_seg;
+    int32_t band0;      // first band (two cell rows) of the replica in the persistent sweep's progress words
     double w, w_below;  // FP64 cell side and the largest double below it
     double L, delta;    // FP64 box side and maximum step (sigma units)
     double Lm;          // realised box side (fixed form: m W 2^-24) for g(r) and eta

@@ -35,6 +35,8 @@ struct LaunchCfg {
     int blocks_tile;   // fused-sweep tile grid size (all replicas)
     int blocks_t32;    // 32 x (threads / 32) cell-tile grid size (all replicas)
     int blocks_seg;    // half-row segment grid size of one colour pass (all replicas)
+    int persist_blocks;  // grid of the persistent sweep (resident blocks), from persist_grid
+    bool persist_stall;  // test hook: the persistent sweep withholds one item and gives up waiting early
     cudaStream_t stream;
 };
 
@@ -77,6 +79,15 @@ cudaError_t launch_pass_tma(const LaunchCfg& c, const Frame* table, int j, int p
 int fused_tile(bool fixed, int cap);
 cudaError_t launch_sweep_fused(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,
                                unsigned long long* counters, int* err);
+// nsweeps <= kMaxChunk sweeps of the draw table in one launch (rebuild and
+// four colour passes per sweep, scheduled as a wavefront over bands of two
+// cell rows), from `from` into `to` for the first sweep and alternating
+// after; sync: persist_sync_words(total_bands) words of device scratch,
+// cleared by the launcher.
+size_t persist_sync_words(int total_bands);
+cudaError_t persist_grid(const LaunchCfg& c, int* blocks);
+cudaError_t launch_sweeps_persist(const LaunchCfg& c, const Frame* table, int nsweeps, CellBufs from, CellBufs to,
+                                  unsigned long long* counters, int* err, uint32_t* sync, int total_bands);
 cudaError_t launch_positions(const LaunchCfg& c, const Frame* cur, CellBufs cells, double* xy);
 // Psi_6 autocorrelation of the measurement series (series[T][R][4]) for lags
 // 0..max_lag into C[R][max_lag + 1], and the correlation time from it.

@@ -1,0 +1,267 @@
+// hd_sweep_cell.cuh -- the per-cell bodies of the checkerboard sweep's
+// rebuild and colour pass (Engel et al., arXiv:1211.1645, Sec. II.B), shared
+// by the split kernels (one launch per rebuild and per colour pass, loads
+// through the read-only path) and the persistent sweep kernel (many sweeps
+// per launch, coherent loads; see ld_cell).
+#pragma once
+
+#include "hd_cell.cuh"
+
+namespace hd {
+
+// Per-thread shared area of the fixed form: 8 neighbours x kEagerSlots slots,
+// plus one pad entry so that a warp's 8-byte accesses take the minimum two
+// shared-memory wavefronts.
+constexpr int kNbrStride = 17;
+
+// ... followed by each thread's area for the occupants of a crowded cell
+// (more than kEagerSlots disks): CAP positions and CAP ids.
+template <bool FIX, int CAP>
+constexpr size_t pass_smem(int threads) {
+    return (FIX ? size_t(threads) * kNbrStride * sizeof(int2) : 0) + size_t(threads) * CAP * (sizeof(P2<FIX>) + 4);
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+
+// Rebuild by scatter of two old cells of one replica (replica-local planar
+// indices a[0], a[1]; live[h] false skips one): each disk is moved into the
+// frame of sweep j (shift difference of tab[j - 1] and tab[j]) and claims a
+// slot of its new cell; the old cells' occupancies are cleared.  The loads of
+// both cells and then the slot claims of both are issued before either is
+// waited on.  Returns true if a new cell overflowed.
+template <bool FIX, int CAP, bool COH>
+__device__ __forceinline__ bool rebuild_pair(const Rep& rep, const Frame* __restrict__ tab, int j, const uint32_t (&a)[2],
+                                             const bool (&live)[2], uint8_t* __restrict__ cnt_o,
+                                             const P2<FIX>* __restrict__ pos_o, const int32_t* __restrict__ pid_o,
+                                             uint8_t* __restrict__ cnt_n, P2<FIX>* __restrict__ pos_n,
+                                             int32_t* __restrict__ pid_n) {
+    const int m = rep.m;
+    uint32_t c[2];
+    int n[2];
+    CellRegs<FIX, true> src[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        c[h] = rep.coff + a[h];
+        n[h] = 0;
+        if (live[h]) {
+            load_cell<FIX, true, CAP, COH>(cnt_o, pos_o, pid_o, rep.stride32, c[h], src[h]);
+            n[h] = src[h].n;
+        }
+    }
+    if (n[0] == 0 && n[1] == 0) return false;
+    const ShiftDelta<FIX> sd(tab[j - 1], tab[j]);
+    // destination and new offsets of the first kEagerSlots disks of both cells
+    uint32_t di[2][kEagerSlots];
+    P2<FIX> nq[2][kEagerSlots];
+    int cxy[2][2];
+    // Fixed point: the shift difference has one sign per axis for the whole
+    // sweep, so a coordinate can only leave its cell on that side (the same
+    // integers as frame_change_fixed, with the impossible branch dropped).
+    auto step_fixed = [&](int32_t d, int c, int32_t u, int& c_out, int32_t& u_out) {
+        int32_t t = u + d;
+        if (d >= 0) {
+            if (t >= rep.W) {
+                t -= rep.W;
+                c = c + 1 == m ? 0 : c + 1;
+            }
+        } else if (t < 0) {
+            t += rep.W;
+            c = c == 0 ? m - 1 : c - 1;
+        }
+        c_out = c;
+        u_out = t;
+    };
+    auto move = [&](const P2<FIX>& q, int cx, int cy, uint32_t& d, P2<FIX>& out) {
+        int tcx, tcy;
+        if constexpr (FIX) {
+            step_fixed(sd.fx, cx, q.x, tcx, out.x);
+            step_fixed(sd.fy, cy, q.y, tcy, out.y);
+        } else {
+            frame_change_fp64(sd.dx, rep.w, rep.w_below, m, cx, q.x, tcx, out.x);
+            frame_change_fp64(sd.dy, rep.w, rep.w_below, m, cy, q.y, tcy, out.y);
+        }
+        d = rep.coff + row_part(rep, tcy) + col_part(rep, tcx);
+    };
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (n[h] == 0) continue;
+        cnt_o[c[h]] = 0;  // leaves this buffer zeroed for the rebuild after next
+        cell_coords(rep, a[h], cxy[h][0], cxy[h][1]);
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k)
+            if (k < n[h]) move(src[h].s[k], cxy[h][0], cxy[h][1], di[h][k], nq[h][k]);
+    }
+    int slot[2][kEagerSlots];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k)
+            if (k < n[h]) slot[h][k] = claim_slot(cnt_n, di[h][k]);
+    bool over = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < kEagerSlots; ++k) {
+            if (k < n[h]) {
+                if (slot[h][k] < CAP) {
+                    pos_n[size_t(slot[h][k]) * rep.stride32 + di[h][k]] = nq[h][k];
+                    pid_n[size_t(slot[h][k]) * rep.stride32 + di[h][k]] = src[h].id[k];
+                } else {
+                    over = true;
+                }
+            }
+        }
+        // crowded old cells (rare): the remaining disks one at a time
+        if (n[h] > kEagerSlots)
+        for (int k = kEagerSlots; k < n[h]; ++k) {
+            uint32_t d;
+            P2<FIX> q;
+            move(src[h].template slot<COH>(k, pos_o, rep.stride32), cxy[h][0], cxy[h][1], d, q);
+            const int s2 = claim_slot(cnt_n, d);
+            if (s2 < CAP) {
+                pos_n[size_t(s2) * rep.stride32 + d] = q;
+                pid_n[size_t(s2) * rep.stride32 + d] = src[h].template slot_id<COH>(k, pid_o, rep.stride32);
+            } else {
+                over = true;
+            }
+        }
+    }
+    return over;
+}
+
+// One active cell of a colour pass: planar index a of colour col in the
+// replica.  Its eight neighbours' occupancies are loaded and, in the fixed
+// form, their first two slots copied into `mine` (this thread's 2 x 8 + 1
+// entries of shared memory) with cp.async, all before the cell itself is
+// loaded and its draws are made, so the generator's arithmetic overlaps the
+// latency.  Then the cell's occupants are shuffled and make rep.nt serial
+// trial moves (try_cell); a cell of more than kEagerSlots disks keeps them in
+// sp / si (this thread's CAP entries of shared memory).  Adds the trials and
+// acceptances to att and acc.  No copy is left in flight on return.
+template <bool FIX, int CAP, int NTC, bool COH>
+__device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int col, uint32_t a,
+                                          const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, int2* mine,
+                                          P2<FIX>* sp, int32_t* si, uint32_t& att, uint32_t& acc) {
+    const int m = rep.m, hm = rep.hm;
+    const uint32_t row = div_by(a, rep.hm_mul, rep.hm_sh);
+    const int cx = 2 * int(a - row * uint32_t(hm)) + (col & 1);
+    const int cy = 2 * int(row) + (col >> 1);
+    const uint32_t cl = uint32_t(cy) * uint32_t(m) + uint32_t(cx);  // Philox counter: row-major cell
+    const uint32_t cell = rep.coff + uint32_t(col) * uint32_t(rep.hh) + a;
+    uint32_t xp[3], yp[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        xp[o] = col_part(rep, wrap_cell(cx + o - 1, m));
+        yp[o] = rep.coff + row_part(rep, wrap_cell(cy + o - 1, m));
+    }
+    // Fixed form: neighbour i (0..8, centre skipped as nbr index q) has its
+    // occupancy in bits 4q..4q+3 of nocc and slots 0, 1 in mine[2q], mine[2q + 1].
+    uint32_t nocc = 0;
+    if constexpr (FIX) {
+        const uint32_t sm = static_cast<uint32_t>(__cvta_generic_to_shared(mine));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) continue;
+            const int q = i < 4 ? i : i - 1;
+            const uint32_t ci = yp[i / 3] + xp[i % 3];
+            nocc |= uint32_t(occupancy<CAP, COH>(cnt, ci)) << (4 * q);
+            cp_async8(sm + uint32_t(2 * q) * 8u, pos + ci);
+            cp_async8(sm + uint32_t(2 * q + 1) * 8u, pos + rep.stride32 + ci);
+        }
+    }
+    CellRegs<FIX, true> own;
+    load_cell<FIX, true, CAP, COH>(cnt, pos, pid, rep.stride32, cell, own);
+    const int n = own.n;
+    if (n > 0) {
+        auto neighbours_clear = [&](const P2<FIX>& np) {
+            bool ok = true;
+            if constexpr (FIX) {
+                cp_async_wait_all();  // a no-op after the first trial
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (i == 4) continue;
+                    const int q = i < 4 ? i : i - 1;
+                    const int ox = i % 3 - 1, oy = i / 3 - 1;
+                    const int ni = int(nocc >> (4 * q)) & 0xF;
+                    ok &= pair_clear<FIX>(mine[2 * q], ox, oy, np, rep) | (ni < 1);
+                    ok &= pair_clear<FIX>(mine[2 * q + 1], ox, oy, np, rep) | (ni < 2);
+                }
+                // Neighbours holding more than kEagerSlots disks (rare): a
+                // nibble n >= 3 is the one whose n + 5 sets its bit 3.
+                if ((nocc + 0x55555555u) & 0x88888888u) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        if (i == 4) continue;
+                        const int q = i < 4 ? i : i - 1;
+                        const int ni = int(nocc >> (4 * q)) & 0xF;
+                        // the cell index is recomputed here, so that no register keeps it
+                        const uint32_t ci = rep.coff + row_part(rep, wrap_cell(cy + i / 3 - 1, m)) +
+                                            col_part(rep, wrap_cell(cx + i % 3 - 1, m));
+                        for (int k = kEagerSlots; k < ni; ++k)
+                            ok &= pair_clear<FIX>(ld_cell<COH>(pos + size_t(k) * rep.stride32 + ci), i % 3 - 1, i / 3 - 1,
+                                                  np, rep);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (i == 4 || !ok) continue;
+                    const int ox = i % 3 - 1, oy = i / 3 - 1;
+                    CellRegs<FIX, false> c;
+                    load_cell<FIX, false, CAP, COH>(cnt, pos, nullptr, rep.stride32, yp[i / 3] + xp[i % 3], c);
+                    for (int k = 0; k < c.n && ok; ++k)
+                        ok = pair_clear<FIX>(c.template slot<COH>(k, pos, rep.stride32), ox, oy, np, rep);
+                }
+            }
+            return ok;
+        };
+        if (n <= kEagerSlots) {
+            // the usual cell: its occupants in registers, in ascending id
+            // (the base order of the shuffle)
+            P2<FIX> P[kEagerSlots] = {own.s[0], own.s[1]};
+            int32_t ids[kEagerSlots] = {own.id[0], own.id[1]};
+            if (n > 1) sort_by_id<FIX, kEagerSlots>(P, ids, n);
+            const uint32_t na = try_cell<FIX, kEagerSlots, NTC>(rep, f.sweep, cl, P, n, neighbours_clear);
+            acc += na;
+            // written back in id order (the ids too, since the sort may have permuted them)
+            if (na > 0 || n > 1) {
+#pragma unroll
+                for (int q = 0; q < kEagerSlots; ++q)
+                    if (q < n) pos[size_t(q) * rep.stride32 + cell] = P[q];
+            }
+            if (n > 1) {
+#pragma unroll
+                for (int q = 0; q < kEagerSlots; ++q)
+                    if (q < n) pid[size_t(q) * rep.stride32 + cell] = ids[q];
+            }
+        } else {
+            // a crowded cell (rare): its occupants in this thread's shared
+            // area, so that the registers stay sized for two
+            for (int q = 0; q < n; ++q) {
+                P2<FIX> v = own.template slot<COH>(q, pos, rep.stride32);
+                int32_t id = own.template slot_id<COH>(q, pid, rep.stride32);
+                int k = q;
+                for (; k > 0 && si[k - 1] > id; --k) {
+                    sp[k] = sp[k - 1];
+                    si[k] = si[k - 1];
+                }
+                sp[k] = v;
+                si[k] = id;
+            }
+            acc += try_cell_in<FIX, CAP, NTC>(rep, f.sweep, cl, SmemCell<FIX>{sp}, n, neighbours_clear);
+            for (int q = 0; q < n; ++q) {
+                pos[size_t(q) * rep.stride32 + cell] = sp[q];
+                pid[size_t(q) * rep.stride32 + cell] = si[q];
+            }
+        }
+        att += uint32_t(rep.nt);
+    }
+    // no copy may still be landing in shared memory when the thread moves on
+    if constexpr (FIX) cp_async_wait_all();
+}
+
+}  // namespace hd

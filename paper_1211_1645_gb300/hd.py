@@ -147,7 +147,7 @@ def hd_default_opts() -> hd_opts:
     return o
 
 
-SWEEP_KERNELS = {"split": 0, "fused": 1, "tma": 2}
+SWEEP_KERNELS = {"split": 0, "fused": 1, "tma": 2, "persistent": 3}
 
 
 def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=50, hist_dr=1e-3,

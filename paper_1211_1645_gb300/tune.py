@@ -6,7 +6,8 @@ ones are cheaper per trial.  The autotuner chooses, by timing graph-captured
 steps of the library on the current GPU:
 
 * for one workload (``autotune``): the minimum cell side, the sweep kernel
-  (split launches or one fused shared-memory launch per sweep), the threads
+  (split launches, one fused shared-memory launch per sweep, or one
+  persistent launch for many sweeps), the threads
   per block of the split kernels and the threads per active cell of the
   split colour pass (1, or a group of 2, 4 or 8 lanes that split the overlap
   tests and combine them with a warp ballot);
@@ -71,7 +72,7 @@ def autotune(N, eta, delta, seed=1, precision="fixed", cell_mins=(2.0, 2.2, 2.4)
     for cm, kern, bt, g in itertools.product(cell_mins, kernels, block_threads, threads_per_cell):
         if kern == "fused" and (bt != block_threads[0] or g != 1):
             continue  # the fused kernel has a fixed block size and one thread per cell
-        if kern == "tma" and g != 1:
+        if kern in ("tma", "persistent") and g != 1:
             continue
         try:
             results.append(time_config(N, eta, delta, seed, precision, cm, kern, bt, sweeps, steps, g))

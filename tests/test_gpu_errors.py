@@ -57,3 +57,27 @@ def test_unaligned_slot_stride_is_valid_for_the_cp_async_pass(hd, oracle_mod, mo
     assert (int(att[0]), int(acc[0])) == o.stats()
     assert np.array_equal(g.positions(), o.positions())
     g.close()
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_persistent_sweep_wait_gives_up_and_sticks(hd, monkeypatch, form):
+    """HD_TEST_PERSIST_STALL=1 at creation: the persistent sweep never
+    publishes the first item of band 0, and its bounded dependency waits give
+    up after 4096 polls instead of waiting forever.  The launch ends, the
+    host reports HD_ERR_TIMEOUT and the context stays in its error state."""
+    from paper_1211_1645_gb300.hd import HD_ERR_STATE, HD_ERR_TIMEOUT, HDError
+    monkeypatch.setenv("HD_TEST_PERSIST_STALL", "1")
+    g = hd.HardDisks(4096, 0.70, 0.1, 3, precision=form, sweep_kernel="persistent")
+    monkeypatch.delenv("HD_TEST_PERSIST_STALL")
+    g.sweep(3)
+    with pytest.raises(HDError) as e:
+        g.stats()
+    assert e.value.status == HD_ERR_TIMEOUT
+    with pytest.raises(HDError) as e:
+        g.sweep(1)
+    assert e.value.status == HD_ERR_STATE
+    g.close()
+    g2 = hd.HardDisks(4096, 0.70, 0.1, 3, precision=form, sweep_kernel="persistent")
+    g2.sweep(3)
+    assert int(g2.stats()[0][0]) > 0
+    g2.close()

@@ -57,14 +57,15 @@ def assert_same_state(g, o):
     assert np.array_equal(g.positions(), o.positions())
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split", "tma", "split-g2", "split-g4", "split-g8"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma", "persistent", "split-g2", "split-g4", "split-g8"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
     """Every sweep kernel: one launch per sweep with shared-memory tiles; a
     rebuild launch plus four colour-pass launches (one thread per active
     cell, bulk-copy staging, or G = 2, 4, 8 threads per cell with a warp
-    ballot over the overlap tests)."""
+    ballot over the overlap tests); one persistent launch per call of up to
+    256 sweeps (a wavefront of band work items)."""
     g, o = make_pair(hd, oracle_mod, form, kernel=kernel, **CASES[case])
     geo, ogeo = g.geometry(), o.geometry()
     assert geo["m"] == ogeo["m"] and geo["L"] == ogeo["L"] and geo["trials_per_cell"] == ogeo["nt"]
@@ -76,7 +77,7 @@ def test_chain_bit_exact(hd, oracle_mod, form, case, kernel):
     g.close()
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma", "persistent"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_chunk_boundary(hd, oracle_mod, form, kernel):
     """More sweeps in one call than one draw table holds (256)."""
@@ -186,7 +187,7 @@ def test_full_size_N65536_liquid(hd, oracle_mod, form):
     assert np.array_equal(hist[0], o.histogram(50, 1e-3))
 
 
-@pytest.mark.parametrize("kernel", ["fused", "split", "tma"])
+@pytest.mark.parametrize("kernel", ["fused", "split", "tma", "persistent"])
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
 def test_full_size_N1048576_coexistence(hd, oracle_mod, form, kernel):
     """N = 1024^2 at eta = 0.716 (coexistence), the benchmark workload: whole
@@ -308,7 +309,7 @@ def test_overflow_rejected_on_set_positions(hd):
     assert e.value.status == HD_ERR_OVERFLOW
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "tma"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "tma", "persistent"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_graph_engine_series(hd, oracle_mod, form, kernel):
     """hd_run: graph-captured steps of 7 sweeps (odd, so both buffer parities
@@ -360,7 +361,7 @@ def test_graph_engine_batched(hd, oracle_mod, form):
         off += Ns[r]
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "tma"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "tma", "persistent"])
 @pytest.mark.parametrize("form", ["fp64", "fixed"])
 def test_checkpoint_resume_bit_exact(hd, oracle_mod, form, kernel):
     """A chain checkpointed after 40 sweeps and restored into a fresh context
@@ -466,5 +467,29 @@ def test_batched_replicas_per_replica_cell_sides(hd, oracle_mod, form):
             assert np.array_equal(xy[off:off + Ns[r]], o.positions())
             _, rglob = o.psi6()
             assert complex(ser[-1, r, 2], ser[-1, r, 3]) == rglob
+            off += Ns[r]
+        g.close()
+
+
+def test_persistent_batched_replicas(hd, oracle_mod):
+    """The persistent sweep over replicas of uneven N (their bands interleave
+    in each phase), graph-captured steps with measurement, against each
+    replica's oracle chain."""
+    for form in ("fixed", "fp64"):
+        Ns = [16 ** 2, 24 ** 2, 32 ** 2, 20 ** 2, 17 ** 2]
+        etas = [0.700, 0.701, 0.702, 0.703, 0.704]
+        seeds = [101, 102, 103, 104, 105]
+        g = hd.HardDisks(Ns, etas, [0.1] * 5, seeds, precision=form, sweep_kernel="persistent")
+        os_ = [oracle_mod.OracleChain(n, e, 0.1, sd, form=form) for n, e, sd in zip(Ns, etas, seeds)]
+        g.run(3, 9, measure=True)
+        g.sweep(5)
+        for o in os_:
+            o.sweep(32)
+        att, acc = g.stats()
+        xy = g.positions()
+        off = 0
+        for r, o in enumerate(os_):
+            assert (int(att[r]), int(acc[r])) == o.stats()
+            assert np.array_equal(xy[off:off + Ns[r]], o.positions())
             off += Ns[r]
         g.close()
