@@ -66,6 +66,8 @@ def parse_args(argv=None):
     p.add_argument("--cell-min", type=float, default=2.0, help="minimum cell side in sigma (>= 2)")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--form", choices=["fixed", "fp64"], default="fixed")
+    p.add_argument("--lattice", choices=["square", "triangular"], default="square",
+                   help="start lattice (triangular: odd rows shifted by half a spacing)")
     p.add_argument("--sweep-kernel", choices=["split", "tma", "fused"], default="split")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-e2e", action="store_true")
@@ -401,10 +403,10 @@ def peaks():
 # CUDA sources each kernel class is compiled from (a recorded ncu traffic
 # figure stays valid while these are unchanged)
 KERNEL_SOURCES = {
-    "pass": ["hd_sweep.cu", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h"],
-    "rebuild": ["hd_sweep.cu", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h"],
-    "draws": ["hd_sweep.cu", "hd_device.cuh", "hd_kernels.h"],
-    "hist": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h"],
+    "pass": ["hd_sweep.cu", "hd_sweep_cell.cuh", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
+    "rebuild": ["hd_sweep.cu", "hd_sweep_cell.cuh", "hd_cell.cuh", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
+    "draws": ["hd_sweep.cu", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
+    "hist": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
     "psi6": ["hd_measure.cu", "hd_device.cuh", "hd_kernels.h", "hd_exact.cuh"],
 }
 
@@ -564,7 +566,7 @@ def run_ours(args):
     hd.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    main = time_form(args, args.form, rank, world, args.steps, args.warmup, sampler)
+    main = time_form(args, args.form, rank, world, args.steps, args.warmup, sampler, lattice=args.lattice)
     tmax, att_sum = reduce_max_sum(world, main["ms"], float(main["attempts"]), dev)
     value = att_sum / (tmax / 1e3)
     fp64 = None
