@@ -461,26 +461,31 @@ _L2_GBS = None
 
 
 def l2_copy_gbs():
-    """Copy bandwidth of data resident in L2, measured here: a 24 MB buffer
-    copied into another (48 MB in all, well inside the 129 MB L2) 200 times
-    after a warm-up, read + write bytes over the CUDA-event time.  The
+    """Copy bandwidth of data resident in L2, measured here: buffers of 4, 8,
+    16 and 24 MB copied into a second buffer of the same size (at most 48 MB
+    in all, well inside the 129 MB L2) 200 times after a warm-up; read +
+    write bytes over the CUDA-event time, the best of the sizes.  The
     denominator of the L2 roof."""
     global _L2_GBS
     if _L2_GBS is None:
         import torch
-        n = 24 << 20
-        a = torch.ones(n, dtype=torch.uint8, device="cuda")
-        b = torch.empty_like(a)
-        for _ in range(20):
-            b.copy_(a)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(200):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize()
-        _L2_GBS = 2 * n * 200 / (e0.elapsed_time(e1) / 1e3) / 1e9
+        best = 0.0
+        for mb in (4, 8, 16, 24):
+            n = mb << 20
+            a = torch.ones(n, dtype=torch.uint8, device="cuda")
+            b = torch.empty_like(a)
+            for _ in range(20):
+                b.copy_(a)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(200):
+                b.copy_(a)
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, 2 * n * 200 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+            del a, b
+        _L2_GBS = best
     return _L2_GBS
 
 
