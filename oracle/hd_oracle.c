@@ -372,8 +372,9 @@ static double cell_off_fp64(const hdo_state *s, int o)
     return o < 0 ? -s->w : (o > 0 ? s->w : 0.0);
 }
 
-/* One active cell: shuffle its occupants, then nt serial trial moves. */
-static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy)
+/* One active cell: shuffle its occupants, then nt serial trial moves; the
+ * trials are added to *attempts, the accepted ones to *accepts. */
+static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy, uint64_t *attempts, uint64_t *accepts)
 {
     int m = s->m;
     int64_t c = (int64_t)ccy * m + ccx;
@@ -414,7 +415,7 @@ static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy)
         uint32_t a[4];
         hdo_philox4x32_10(ctr, s->key, a);
         int64_t i = ids[perm[t % n]];
-        s->attempts++;
+        (*attempts)++;
         int overlap = 0;
         if (s->form == HDO_FP64) {
             uint64_t kx = ((uint64_t)(a[0] >> 6) << 27) | (uint64_t)(a[1] >> 5);
@@ -443,7 +444,7 @@ static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy)
             if (!overlap) {
                 s->ux[i] = nx;
                 s->uy[i] = ny;
-                s->accepts++;
+                (*accepts)++;
             }
         } else {
             int64_t dX = (int64_t)bounded(a[0], (uint32_t)(2 * s->D + 1)) - s->D;
@@ -466,7 +467,7 @@ static void update_cell(hdo_state *s, uint32_t sweep32, int ccx, int ccy)
             if (!overlap) {
                 s->fx[i] = (int32_t)nx;
                 s->fy[i] = (int32_t)ny;
-                s->accepts++;
+                (*accepts)++;
             }
         }
     }
@@ -510,7 +511,7 @@ void hdo_sweep(hdo_state *s, int64_t nsweeps)
             int col = perm[p];
             for (int ccy = (col >> 1); ccy < m; ccy += 2)
                 for (int ccx = (col & 1); ccx < m; ccx += 2)
-                    update_cell(s, (uint32_t)sweep, ccx, ccy);
+                    update_cell(s, (uint32_t)sweep, ccx, ccy, &s->attempts, &s->accepts);
         }
         s->sweep = sweep + 1;
     }
