@@ -69,6 +69,41 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_OMP_SRC = os.path.join(_HERE, "hd_oracle_omp.c")
+_OMP_SO = os.path.join(_HERE, "_build", "libhd_oracle_omp.so")
+_omp_lib = None
+
+
+def build_omp(force: bool = False) -> str | None:
+    """Compile the OpenMP sweep (hd_oracle_omp.c, which includes the oracle's
+    own source) with gcc -fopenmp; None when the compiler has no OpenMP."""
+    os.makedirs(os.path.dirname(_OMP_SO), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_OMP_SRC))
+    if force or not os.path.exists(_OMP_SO) or os.path.getmtime(_OMP_SO) < newest:
+        tmp = _OMP_SO + f".tmp{os.getpid()}"
+        r = subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                            "-fopenmp", "-Wall", "-o", tmp, _OMP_SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _OMP_SO)
+    return _OMP_SO
+
+
+def _load_omp():
+    """The OpenMP library, or None.  It shares the state layout of the oracle
+    (the same source), so it advances the oracle's own chains."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            so = build_omp()
+            if so is None:
+                return None
+            lib = ctypes.CDLL(so)
+            lib.hdo_sweep_omp.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+            _omp_lib = lib
+        return _omp_lib
+
+
 def _load():
     global _lib
     with _lock:
@@ -140,6 +175,15 @@ class OracleChain:
 
     def sweep(self, n: int = 1) -> None:
         _load().hdo_sweep(self._h, int(n))
+
+    def sweep_omp(self, n: int = 1, threads: int = 0) -> bool:
+        """The same n sweeps with each colour's cells shared out between
+        `threads` host threads (0: all); False when OpenMP is unavailable."""
+        lib = _load_omp()
+        if lib is None:
+            return False
+        lib.hdo_sweep_omp(self._h, int(n), int(threads))
+        return True
 
     def positions(self) -> np.ndarray:
         out = np.empty((self.N, 2), dtype=np.float64)

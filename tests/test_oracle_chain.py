@@ -179,3 +179,19 @@ def test_eight_disks_against_rejection_sampling(oracle_mod, form):
             want_se = np.sqrt(want * (1 - want) / len(ref))
             mean, se = batch_se(mc[:, col] <= R)
             assert abs(mean - want) < 5 * np.hypot(se, want_se) + 2e-3, (col, R, mean, want, se)
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_openmp_sweep_is_the_same_chain(oracle_mod, form):
+    """The all-cores sweep (each colour's cells shared out between threads)
+    is bit-identical to the sequential oracle: positions and trial counts."""
+    a = oracle_mod.OracleChain(4096, 0.70, 0.12, 5, form=form)
+    b = oracle_mod.OracleChain(4096, 0.70, 0.12, 5, form=form)
+    if not b.sweep_omp(1, 4):
+        pytest.skip("no OpenMP in this compiler")
+    a.sweep(1)
+    for n in (6, 13):
+        a.sweep(n)
+        b.sweep_omp(n, 4)
+        assert a.stats() == b.stats()
+        assert np.array_equal(a.positions(), b.positions())
