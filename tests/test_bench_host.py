@@ -115,3 +115,50 @@ def test_recorded_profile_figures_follow_kernel_sources(tmp_path, monkeypatch):
         f.write("\n// changed\n")
     assert bench.recorded_traffic("pass", w) is None
     assert bench.recorded_counters("pass", w) is None
+
+
+def test_in_step_times_fill_the_step():
+    """Each kernel class is charged its share of the profiled event times x
+    the graph-timed step, so the classes add up to ms_per_step whichever way
+    the event times over- or under-shoot it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    run = {"kernel_times": {"pass": (8.0, 800), "rebuild": (2.0, 200), "psi6": (0.4, 2), "hist": (0.0, 0)}}
+    for ms_step in (4.0, 20.0):
+        per, n, total, scale = bench.in_step_times(run, ms_step)
+        assert set(per) == {"pass", "rebuild", "psi6"} and n["pass"] == 400
+        assert abs(sum(v * scale for v in per.values()) - ms_step) < 1e-12
+        assert abs(per["pass"] * scale / n["pass"] - ms_step * 8.0 / 10.4 / 400) < 1e-15
+
+
+def test_roofline_picks_the_binding_roof(monkeypatch):
+    """The top-level roof is the one the committed counters show closest to
+    saturation: issue (alu) when issue-active leads, HBM when DRAM leads;
+    the rates follow from the in-step time per launch."""
+    sys.path.insert(0, ROOT)
+    import bench
+    torch = pytest.importorskip("torch")
+
+    class Props:
+        multi_processor_count = 152
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: Props())
+    monkeypatch.setattr(bench, "l2_copy_gbs", lambda: 8000.0)
+    monkeypatch.setattr(bench, "peaks", lambda: (6800.0, "measured"))
+    monkeypatch.setattr(bench, "recorded_traffic", lambda k, w: 123)
+    counters = {"dram_pct": 20.0, "l2_pct": 13.0, "issue_active_pct": 41.0, "warp_instructions": 5.0e6}
+    monkeypatch.setattr(bench, "recorded_counters", lambda k, w: dict(counters))
+    per, nl = {"pass": 5.0, "rebuild": 1.0}, {"pass": 400.0, "rebuild": 100.0}
+    N, m = 1 << 20, 1072
+    r = bench.roofline(per, nl, 0.7, 4.2, N, m, "fixed", {"sm_mhz": 2000.0}, "x")
+    t = 5.0 * 0.7 / 400 / 1e3
+    assert r["kernel"] == "pass" and r["bound"] == "alu"
+    assert abs(r["issue"]["achieved"] - 5.0e6 / t / 1e9) < 1e-6
+    assert abs(r["issue"]["peak"] - 152 * 4 * 2000.0 * 1e6 / 1e9) < 1e-9
+    alg = bench.algorithmic_bytes("pass", N, m, "fixed")
+    assert alg == m * m + N * 8 + (N // 4) * 8
+    assert abs(r["hbm"]["achieved"] - alg / t / 1e9) < 1e-6 and r["frac"] == r["issue"]["frac"]
+    counters.update(dram_pct=60.0)
+    r = bench.roofline(per, nl, 0.7, 4.2, N, m, "fixed", {"sm_mhz": 2000.0}, "x")
+    assert r["bound"] == "hbm" and r["frac"] == r["hbm"]["frac"] and r["traffic"] == 123
