@@ -148,15 +148,32 @@ __device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int co
                                           P2<FIX>* sp, int32_t* si, uint32_t& att, uint32_t& acc) {
     const int m = rep.m, hm = rep.hm;
     const uint32_t row = div_by(a, rep.hm_mul, rep.hm_sh);
-    const int cx = 2 * int(a - row * uint32_t(hm)) + (col & 1);
-    const int cy = 2 * int(row) + (col >> 1);
+    const int X = int(a - row * uint32_t(hm));
+    const int px = col & 1, py = col >> 1;
+    const int cx = 2 * X + px;
+    const int cy = 2 * int(row) + py;
     const uint32_t cl = uint32_t(cy) * uint32_t(m) + uint32_t(cx);  // Philox counter: row-major cell
     const uint32_t cell = rep.coff + uint32_t(col) * uint32_t(rep.hh) + a;
+    // Column and row parts of the neighbour indices: the columns cx - 1, cx + 1
+    // have parity 1 - px and half-columns X - 1 + px, X + px (periodically),
+    // the rows cy -+ 1 parity 1 - py and half-rows row - 1 + py, row + py.
     uint32_t xp[3], yp[3];
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-        xp[o] = col_part(rep, wrap_cell(cx + o - 1, m));
-        yp[o] = rep.coff + row_part(rep, wrap_cell(cy + o - 1, m));
+    {
+        const uint32_t hh = uint32_t(rep.hh), hmu = uint32_t(hm);
+        int hl = X - 1 + px, hr = X + px;
+        hl = hl < 0 ? hl + hm : hl;
+        hr = hr >= hm ? hr - hm : hr;
+        const uint32_t xo = uint32_t(1 - px) * hh;
+        xp[0] = xo + uint32_t(hl);
+        xp[1] = uint32_t(px) * hh + uint32_t(X);
+        xp[2] = xo + uint32_t(hr);
+        int rl = int(row) - 1 + py, rr = int(row) + py;
+        rl = rl < 0 ? rl + hm : rl;
+        rr = rr >= hm ? rr - hm : rr;
+        const uint32_t yo = rep.coff + uint32_t(1 - py) * 2u * hh;
+        yp[0] = yo + uint32_t(rl) * hmu;
+        yp[1] = rep.coff + uint32_t(py) * 2u * hh + row * hmu;
+        yp[2] = yo + uint32_t(rr) * hmu;
     }
     // Fixed form: neighbour i (0..8, centre skipped as nbr index q) has its
     // occupancy in bits 4q..4q+3 of nocc and slots 0, 1 in mine[2q], mine[2q + 1].
