@@ -209,19 +209,19 @@ __device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int co
                 }
                 // Neighbours holding more than kEagerSlots disks (rare): a
                 // nibble n >= 3 is the one whose n + 5 sets its bit 3.
-                if ((nocc + 0x55555555u) & 0x88888888u) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        if (i == 4) continue;
-                        const int q = i < 4 ? i : i - 1;
-                        const int ni = int(nocc >> (4 * q)) & 0xF;
-                        // the cell index is recomputed here, so that no register keeps it
-                        const uint32_t ci = rep.coff + row_part(rep, wrap_cell(cy + i / 3 - 1, m)) +
-                                            col_part(rep, wrap_cell(cx + i % 3 - 1, m));
-                        for (int k = kEagerSlots; k < ni; ++k)
-                            ok &= pair_clear<FIX>(ld_cell<COH>(pos + size_t(k) * rep.stride32 + ci), i % 3 - 1, i / 3 - 1,
-                                                  np, rep);
-                    }
+                // Only those neighbours are visited (bit 4q + 3 of the mask):
+                // nearly every warp has a lane with one, but a lane rarely
+                // has more than one.
+                for (uint32_t cm = (nocc + 0x55555555u) & 0x88888888u; cm != 0u; cm &= cm - 1u) {
+                    const int q = (__ffs(int(cm)) - 1) >> 2;
+                    const int i = q + (q >= 4 ? 1 : 0);
+                    const int ox = int((0x24924u >> (2 * i)) & 3u) - 1;  // i % 3 - 1
+                    const int oy = int((0x2A540u >> (2 * i)) & 3u) - 1;  // i / 3 - 1
+                    const int ni = int(nocc >> (4 * q)) & 0xF;
+                    // the cell index is recomputed here, so that no register keeps it
+                    const uint32_t ci = rep.coff + row_part(rep, wrap_cell(cy + oy, m)) + col_part(rep, wrap_cell(cx + ox, m));
+                    for (int k = kEagerSlots; k < ni; ++k)
+                        ok &= pair_clear<FIX>(ld_cell<COH>(pos + size_t(k) * rep.stride32 + ci), ox, oy, np, rep);
                 }
             } else {
 #pragma unroll
