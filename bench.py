@@ -308,7 +308,9 @@ def time_extras(args, rank, world, dev):
             "vs_default": (a / (t / 1e3)) / out["scan31"]["value"],
             "choice": {"cell_min_per_replica": choice["cell_min"], "block_threads": choice["block_threads"],
                        "threads_per_cell": choice["threads_per_cell"]},
-            "candidates": stable}
+            "candidates": [{"cell_min_per_replica": c["cell_min"] if len(set(c["cell_min"])) > 1 else c["cell_min"][0],
+                            "block_threads": c["block_threads"], "threads_per_cell": c["threads_per_cell"],
+                            "trial_moves_per_s": c["trial_moves_per_s"]} for c in stable]}
     best, table = autotune(args.N, args.eta, args.delta, args.seed + rank, precision=args.form,
                            cell_mins=(2.0, 2.2, 2.4), kernels=("split", "persistent"), block_threads=(128, 256),
                            threads_per_cell=(1, 2, 4), sweeps=args.sweeps_per_step, steps=2)

@@ -16,10 +16,13 @@ steps of the library on the current GPU:
   replica's own cell side, timed on that replica alone, then the threads per
   block and per cell of the whole batch with those cell sides.
 
-Every candidate runs the same chain definition, so only speed is compared;
-the trial count per step is read back from the library, so a candidate that
-makes cheaper (e.g. more often rejected) trials is not favoured unduly --
-only attempted trial moves per second count.  The step size delta is tuned
+The objective is attempted trial moves per second, read back from the
+library, so a candidate that makes cheaper (e.g. more often rejected) trials
+is not favoured unduly.  A larger cell side is a valid cell system with the
+same equilibrium, but with n_t = ceil(N / m^2) trials per occupied cell it
+can make two serial trials per cell, which raise the trial rate without
+decorrelating the configuration as fast; compare such choices by the Psi_6
+correlation time per second (hd_psi6_tau), not by trial moves alone.  The step size delta is tuned
 separately, toward an acceptance target (hd_tune_delta), because it changes
 the chain's dynamics rather than its speed.
 """
@@ -89,10 +92,13 @@ def autotune_replicas(Ns, etas, delta, seed=1, precision="fixed", cell_mins=(2.0
     Stage 1: for each distinct state point (N, eta) of the batch, every cell
     side in `cell_mins` is timed on a single-replica context (split kernel,
     128 threads); the fastest is that replica's cell side.  Stage 2: the whole
-    batch, with those cell sides, is timed for every (block_threads,
-    threads_per_cell) candidate.  Returns (choice, table) where choice holds
-    the per-replica "cell_min" list, "block_threads", "threads_per_cell" and
-    the batch's "trial_moves_per_s", and table the stage-2 results."""
+    batch is timed with those cell sides, and with the first cell side for
+    every replica (a batch runs one kernel specialisation, and a replica whose
+    cells make two trials each takes the whole batch off the one-trial one),
+    for every (block_threads, threads_per_cell) candidate.  Returns (choice,
+    table) where choice holds the per-replica "cell_min" list,
+    "block_threads", "threads_per_cell" and the batch's "trial_moves_per_s",
+    and table the stage-2 results."""
     R = len(Ns)
     deltas = list(delta) if np.ndim(delta) else [float(delta)] * R
     per_point = {}
@@ -106,18 +112,22 @@ def autotune_replicas(Ns, etas, delta, seed=1, precision="fixed", cell_mins=(2.0
             if r["trial_moves_per_s"] > best_rate:
                 best, best_rate = cm, r["trial_moves_per_s"]
         per_point[(n, e)] = best if best is not None else 2.0
-    cms = [per_point[(n, e)] for n, e in zip(Ns, etas)]
+    # the batch runs one kernel specialisation for all replicas: cell sides
+    # that give some replica two trials per occupied cell can slow the whole
+    # batch, so the uniform first cell side is a candidate too
+    layouts = [[per_point[(n, e)] for n, e in zip(Ns, etas)]]
+    if any(c != cell_mins[0] for c in layouts[0]):
+        layouts.append([cell_mins[0]] * R)
     seeds = [seed + r for r in range(R)]
     table = []
-    for bt, g in itertools.product(block_threads, threads_per_cell):
+    for cms, bt, g in itertools.product(layouts, block_threads, threads_per_cell):
         try:
             t = time_config(list(Ns), list(etas), deltas, seeds, precision, cms, "split", bt, sweeps, steps, g)
         except Exception:
             continue
-        table.append({"block_threads": bt, "threads_per_cell": g, "trial_moves_per_s": t["trial_moves_per_s"]})
+        table.append({"cell_min": cms, "block_threads": bt, "threads_per_cell": g,
+                      "trial_moves_per_s": t["trial_moves_per_s"]})
     table.sort(key=lambda r: -r["trial_moves_per_s"])
     if not table:
         return None, table
-    choice = dict(table[0])
-    choice["cell_min"] = cms
-    return choice, table
+    return dict(table[0]), table
