@@ -593,11 +593,15 @@ def run_ours(args):
     value = att_sum / (tmax / 1e3)
     fp64 = None
     if not args.no_fp64 and args.form != "fp64":
-        r = time_form(args, "fp64", rank, world, max(1, args.steps // 2), 1)
+        s64 = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        steps64 = max(1, args.steps // 2)
+        r = time_form(args, "fp64", rank, world, steps64, max(3, args.warmup), s64, lattice=args.lattice)
         t64, a64 = reduce_max_sum(world, r["ms"], float(r["attempts"]), dev)
-        fp64 = {"value": a64 / (t64 / 1e3), "ms_per_step": t64 / max(1, args.steps // 2),
-                "kernel_ms_per_step": (lambda p, n, t, sc: {k: v * sc for k, v in p.items()})(
-                    *in_step_times(r, t64 / max(1, args.steps // 2)))}
+        p64, n64, _, sc64 = in_step_times(r, t64 / steps64)
+        fp64 = {"value": a64 / (t64 / 1e3), "ms_per_step": t64 / steps64, "steps": steps64,
+                "kernel_ms_per_step": {k: v * sc64 for k, v in p64.items()}, "clocks": r["clocks"],
+                "roofline": roofline(p64, n64, sc64, t64 / steps64, args.N, r["geometry"]["m"], "fp64", r["clocks"],
+                                     f"{args.N}_fp64")}
     # the sweep loop alone (rebuild + four colour passes per sweep), same timing
     so = time_form(args, args.form, rank, world, max(1, args.steps // 2), 2, measure=0)
     tso, aso = reduce_max_sum(world, so["ms"], float(so["attempts"]), dev)
