@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hd.h"
 #include "hd_kernels.h"
 #include "hd_analysis.h"
@@ -20,6 +22,15 @@ using hd::Frame;
 using hd::Rep;
 
 namespace {
+
+// An NVTX range around a public call, so that a profiler (ncu --nvtx, nsys)
+// can select or label the library's phases; a no-op without a profiler.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kFx = 16777216.0;  // 2^24 fixed-point units per sigma
@@ -548,6 +559,7 @@ const char* hd_status_string(hd_status s) {
 
 hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double* eta, double sigma,
                         const double* delta, const uint64_t* seed, const hd_opts* opts_in) {
+    const Range range("hd_batch_init");
     if (!out) return HD_ERR_ARG;
     *out = nullptr;
     if (R < 1 || R > 65535 || !N || !eta || !delta || !seed) return HD_ERR_ARG;
@@ -828,6 +840,7 @@ hd_status hd_set_stream(hd_ctx* ctx, void* stream) {
 }
 
 hd_status hd_sweep(hd_ctx* ctx, int64_t n) {
+    const Range range("hd_sweep");
     if (!ctx || n < 0) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     HD_CK(ctx, enqueue_sweeps(ctx, ctx->stream, n, false));
@@ -836,6 +849,7 @@ hd_status hd_sweep(hd_ctx* ctx, int64_t n) {
 }
 
 hd_status hd_pressure(hd_ctx* ctx, double* betaP_over_rho, double* g_contact, uint64_t* hist) {
+    const Range range("hd_pressure");
     if (!ctx) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     for (const Rep& r : ctx->reps)
@@ -857,6 +871,7 @@ hd_status hd_pressure(hd_ctx* ctx, double* betaP_over_rho, double* g_contact, ui
 }
 
 hd_status hd_psi6(hd_ctx* ctx, double* re, double* im, double* local) {
+    const Range range("hd_psi6");
     if (!ctx) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     HD_CK(ctx, enqueue_psi6(ctx, ctx->stream, local != nullptr, false));
@@ -894,6 +909,7 @@ hd_status hd_positions_device(hd_ctx* ctx, double* xy_device) {
 }
 
 hd_status hd_positions(hd_ctx* ctx, double* xy) {
+    const Range range("hd_positions");
     if (!ctx || !xy) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     HD_CK(ctx, launch(ctx, HD_K_POSITIONS, [&] { return hd::launch_positions(ctx->cfg(), ctx->frame, ctx->buf[ctx->cur], ctx->xy); }));
@@ -904,6 +920,7 @@ hd_status hd_positions(hd_ctx* ctx, double* xy) {
 }
 
 hd_status hd_set_positions(hd_ctx* ctx, const double* xy) {
+    const Range range("hd_set_positions");
     if (!ctx || !xy) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     // upload, then bin on the device into the other generation; switch to it
@@ -985,6 +1002,7 @@ hd_status hd_series_reserve(hd_ctx* ctx, int64_t steps) {
 }
 
 hd_status hd_run(hd_ctx* ctx, int64_t steps, int32_t sweeps_per_step, int32_t measure) {
+    const Range range("hd_run");
     if (!ctx || steps < 0 || sweeps_per_step < 0 || (sweeps_per_step == 0 && !measure) || ctx->R > 1024 ||
         measure < 0 || measure > 2)
         return HD_ERR_ARG;
@@ -1191,6 +1209,7 @@ hd_status hd_set_delta(hd_ctx* ctx, const double* delta) {
 }
 
 hd_status hd_tune_delta(hd_ctx* ctx, double target, int32_t sweeps_per_probe, int32_t probes, double* delta_out) {
+    const Range range("hd_tune_delta");
     if (!ctx || !(target > 0.0 && target < 1.0) || sweeps_per_probe < 1 || probes < 1) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     const int R = ctx->R;
@@ -1237,6 +1256,7 @@ hd_status hd_checkpoint_size(hd_ctx* ctx, size_t* bytes) {
 }
 
 hd_status hd_checkpoint(hd_ctx* ctx, void* buf, size_t bytes) {
+    const Range range("hd_checkpoint");
     if (!ctx || !buf || bytes < checkpoint_bytes(ctx)) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1269,6 +1289,7 @@ hd_status hd_checkpoint(hd_ctx* ctx, void* buf, size_t bytes) {
 }
 
 hd_status hd_restore(hd_ctx* ctx, const void* buf, size_t bytes) {
+    const Range range("hd_restore");
     if (!ctx || !buf || bytes < checkpoint_bytes(ctx)) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     CkHeader want, got;
@@ -1393,6 +1414,7 @@ hd_status hd_psi6_tau(hd_ctx* ctx, int64_t lag_lo, int64_t lag_hi, double* tau) 
 }
 
 hd_status hd_psi6_field(hd_ctx* ctx, int32_t bins, double* field) {
+    const Range range("hd_psi6_field");
     if (!ctx || !field || bins < 1 || bins > 65536) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     const size_t need = size_t(ctx->R) * size_t(bins) * size_t(bins);
@@ -1457,6 +1479,7 @@ hd_status enqueue_sq(hd_ctx* ctx, int nq) {
 }  // namespace
 
 hd_status hd_structure_factor(hd_ctx* ctx, int32_t nq, const int32_t* hk, double* S) {
+    const Range range("hd_structure_factor");
     if (!ctx || !hk || !S || nq < 1 || nq > 65536) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     hd_status st = grow(ctx, ctx->sq_hk, ctx->sq_cap, size_t(ctx->R) * nq);
@@ -1470,6 +1493,7 @@ hd_status hd_structure_factor(hd_ctx* ctx, int32_t nq, const int32_t* hk, double
 }
 
 hd_status hd_positional_q0(hd_ctx* ctx, int32_t half_width, int32_t* hk0, double* S0) {
+    const Range range("hd_positional_q0");
     if (!ctx || !hk0 || half_width < 0 || half_width > 64) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     const int w = 2 * half_width + 1, nq = w * w;
@@ -1515,6 +1539,7 @@ hd_status enqueue_chi(hd_ctx* ctx, const int32_t* hk0) {
 }  // namespace
 
 hd_status hd_positional_field(hd_ctx* ctx, const int32_t* hk0, int32_t bins, double* field) {
+    const Range range("hd_positional_field");
     if (!ctx || !hk0 || !field || bins < 1 || bins > 65536) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     const size_t need = size_t(ctx->R) * size_t(bins) * size_t(bins);
@@ -1540,6 +1565,7 @@ hd_status hd_positional_field(hd_ctx* ctx, const int32_t* hk0, int32_t bins, dou
 }
 
 hd_status hd_positional_corr(hd_ctx* ctx, const int32_t* hk0, int32_t nr, double dr, double* C) {
+    const Range range("hd_positional_corr");
     if (!ctx || !hk0 || !C || nr < 1 || nr > 1024 || !(dr > 0.0)) return HD_ERR_ARG;
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     // cell reach that holds every pair within the largest window, r_nr + 1 (sigma units)

@@ -527,3 +527,17 @@ def test_config1_full_run(hd, oracle_mod, form):
     assert_same_state(g, o)
     att, acc = g.stats()
     assert 0.3 < int(acc[0]) / int(att[0]) < 0.9
+
+
+@pytest.mark.parametrize("lattice", ["square", "triangular"])
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_psi6_on_the_start_lattice(hd, oracle_mod, form, lattice):
+    """The untouched start lattice, where neighbour distances tie everywhere:
+    the six-neighbour list's (r^2, id) order decides psi_j, on the GPU as in
+    the oracle (square: two of the four tied diagonals by smaller id)."""
+    g, o = make_pair(hd, oracle_mod, form, 1024, 0.60, 0.1, 3, lattice=lattice)
+    glob, loc = g.psi6()
+    rloc, rglob = o.psi6()
+    assert np.array_equal(loc, rloc)
+    assert glob[0] == rglob
+    g.close()

@@ -113,3 +113,29 @@ def test_exact_mean_keeps_small_terms():
     for v in z.real[:1000]:
         naive += v
     assert naive == 1.0
+
+
+@pytest.mark.parametrize("form", ["fp64", "fixed"])
+def test_square_lattice_ties_broken_by_id(oracle_mod, form):
+    """A square lattice: four nearest neighbours at 0, 90, 180, 270 degrees
+    contribute exp(6i phi) = 1, -1, 1, -1 (sum 0), and the 5th and 6th are two
+    of the four diagonal neighbours, all at the same distance: the tie rule
+    (smaller id first) picks the two of smallest id.  Diagonals at 45 / 225
+    degrees give exp(6i phi) = -i, at 135 / 315 degrees +i; so psi_j is the
+    mean of those two picks, computed here from the lattice indices alone."""
+    n = 16
+    N = n * n
+    o = oracle_mod.OracleChain(N, 0.5, 0.1, 1, form=form)  # square start lattice, no sweep
+    L = o.geometry()["L"]
+    xy = o.positions()
+    a = L / n
+    col = np.rint(xy[:, 0] / a - 0.5).astype(int) % n
+    row = np.rint(xy[:, 1] / a - 0.5).astype(int) % n
+    idx = {(int(c), int(r)): i for i, (c, r) in enumerate(zip(col, row))}
+    loc, _ = o.psi6()
+    for i in range(N):
+        c, r = int(col[i]), int(row[i])
+        diag = [(idx[((c + dx) % n, (r + dy) % n)], dx, dy) for dx in (-1, 1) for dy in (-1, 1)]
+        diag.sort()
+        val = sum((-1j if dx * dy > 0 else 1j) for _, dx, dy in diag[:2]) / 6
+        assert abs(loc[i] - val) < (1e-12 if form == "fp64" else 1e-6), (i, loc[i], val)
