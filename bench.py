@@ -170,7 +170,8 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # the GPU arm
 # ---------------------------------------------------------------------------
 def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
-              block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None, threads_per_cell=1):
+              block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None, threads_per_cell=1,
+              keep_positions=False):
     """Device-resident timing of `steps` steps of one form; returns a dict.
     N and eta may be per-replica lists (one batched context); attempts are
     summed over replicas.  measure: 0 sweeps only, 1 pressure and Psi_6 per
@@ -243,10 +244,11 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
     sysg.profile(False)
     geo = sysg.geometry()
     series = sysg.series()
+    final_xy = sysg.positions() if keep_positions else None
     sysg.close()
     return {"ms": ms, "steps": steps, "attempts": attempts, "launches": launches, "clocks": clocks,
             "kernel_times": kt, "geometry": geo, "last_measurement": series[-1, 0].tolist() if len(series) else None,
-            "acceptance": acceptance}
+            "acceptance": acceptance, "final_xy": final_xy}
 
 
 PROFILED_STEPS = 2
@@ -328,21 +330,24 @@ def time_extras(args, rank, world, dev):
     return out
 
 
-def time_e2e(args, form, rank, steps):
+def time_e2e(args, form, rank, steps, xy0):
     """Same metric through the public API with host buffers: each step uploads
     the step's input configuration from pinned host memory (hd_set_positions:
     copy and binning on the device), runs the sweeps (hd_run, one graph
     launch) and reads the step's result back (the contact pressure and
-    Psi_6, hd_pressure and hd_psi6)."""
+    Psi_6, hd_pressure and hd_psi6).  The input is xy0, the configuration the
+    device-timed leg ended in, so that both legs time the same state (trial
+    moves per sweep are the occupied cells, which a fresh lattice has more
+    of than a relaxed configuration)."""
     import numpy as np
     import torch
 
     import paper_1211_1645_gb300 as hd
 
     sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form, cell_min=args.cell_min)
-    pinned = torch.empty((sysg.positions().shape[0], 2), dtype=torch.float64, pin_memory=True)
+    pinned = torch.empty((xy0.shape[0], 2), dtype=torch.float64, pin_memory=True)
     xy = pinned.numpy()
-    xy[:] = sysg.positions()
+    xy[:] = xy0
     S = args.sweeps_per_step
     sysg.run(1, S, False)  # capture the step's graph before timing
     torch.cuda.synchronize()
@@ -358,7 +363,7 @@ def time_e2e(args, form, rank, steps):
     attempts = int(sysg.stats()[0][0]) - att0
     sysg.close()
     return {"value": attempts / dt, "unit": UNIT, "h2d_bytes_per_step": int(xy.nbytes),
-            "d2h_bytes_per_step": 8 * 4 + 4 * 2}
+            "d2h_bytes_per_step": 8 * 4 + 4 * 2, "input": "the device-timed leg's final configuration, every step"}
 
 
 def algorithmic_bytes(kernel, N, m, form):
@@ -588,7 +593,8 @@ def run_ours(args):
     hd.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    main = time_form(args, args.form, rank, world, args.steps, args.warmup, sampler, lattice=args.lattice)
+    main = time_form(args, args.form, rank, world, args.steps, args.warmup, sampler, lattice=args.lattice,
+                     keep_positions=not args.no_e2e)
     tmax, att_sum = reduce_max_sum(world, main["ms"], float(main["attempts"]), dev)
     value = att_sum / (tmax / 1e3)
     fp64 = None
@@ -609,7 +615,7 @@ def run_ours(args):
                    "config": f"{args.sweeps_per_step} sweeps per step, no measurement"}
     e2e = None
     if not args.no_e2e:
-        e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2))
+        e2e = time_e2e(args, args.form, rank, max(1, args.steps // 2), main["final_xy"])
     extras = None if args.no_extras else time_extras(args, rank, world, dev)
     c5 = None if args.no_extras else time_config5(args, rank, world, dev)
     if rank != 0:
