@@ -69,6 +69,8 @@ def parse_args(argv=None):
     p.add_argument("--lattice", choices=["square", "triangular"], default="square",
                    help="start lattice (triangular: odd rows shifted by half a spacing)")
     p.add_argument("--sweep-kernel", choices=["split", "tma", "fused"], default="split")
+    p.add_argument("--strips", type=int, default=0,
+                   help="graph wavefront strips of a one-replica step (0: the library's choice, 1: none)")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the replica, scan and autotuned lines")
@@ -171,7 +173,7 @@ def reduce_max_sum(world, tmax: float, tsum: float, device):
 # ---------------------------------------------------------------------------
 def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=None, cell_min=None,
               block_threads=128, sweep_kernel=None, measure=1, lattice="square", sweeps=None, threads_per_cell=1,
-              keep_positions=False):
+              keep_positions=False, strips=None):
     """Device-resident timing of `steps` steps of one form; returns a dict.
     N and eta may be per-replica lists (one batched context); attempts are
     summed over replicas.  measure: 0 sweeps only, 1 pressure and Psi_6 per
@@ -191,7 +193,7 @@ def time_form(args, form, rank, world, steps, warmup, sampler=None, N=None, eta=
         sysg = hd.HardDisks(N, eta, args.delta, args.seed + rank, precision=form,
                             sweep_kernel=sweep_kernel or args.sweep_kernel, lattice=lattice,
                             cell_min=cell_min or args.cell_min, block_threads=block_threads,
-                            threads_per_cell=threads_per_cell)
+                            threads_per_cell=threads_per_cell, strips=args.strips if strips is None else strips)
     else:
         R = len(N)
         seeds = [args.seed + rank * R + r for r in range(R)]
@@ -315,18 +317,16 @@ def time_extras(args, rank, world, dev):
                             "trial_moves_per_s": c["trial_moves_per_s"]} for c in stable]}
     best, table = autotune(args.N, args.eta, args.delta, args.seed + rank, precision=args.form,
                            cell_mins=(2.0, 2.2, 2.4), kernels=("split", "persistent"), block_threads=(128, 256),
-                           threads_per_cell=(1, 2, 4), sweeps=args.sweeps_per_step, steps=2)
+                           threads_per_cell=(1, 2), strips=(1, 8, 16, 24), sweeps=args.sweeps_per_step, steps=2)
     if best:
         rt = time_form(args, args.form, rank, world, steps, warm, cell_min=best["cell_min"],
                        block_threads=best["block_threads"], sweep_kernel=best["sweep_kernel"],
-                       threads_per_cell=best["threads_per_cell"])
+                       threads_per_cell=best["threads_per_cell"], strips=best["strips"])
         t, a = reduce_max_sum(world, rt["ms"], float(rt["attempts"]), dev)
+        keys = ("cell_min", "sweep_kernel", "block_threads", "threads_per_cell", "strips")
         out["autotuned"] = {"value": a / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps,
-                            "choice": {k: best[k] for k in ("cell_min", "sweep_kernel", "block_threads",
-                                                            "threads_per_cell", "cells_per_side", "trials_per_cell")},
-                            "candidates": [{k: c[k] for k in ("cell_min", "sweep_kernel", "block_threads",
-                                                              "threads_per_cell", "trial_moves_per_s")}
-                                           for c in table]}
+                            "choice": {k: best[k] for k in keys + ("cells_per_side", "trials_per_cell")},
+                            "candidates": [{k: c[k] for k in keys + ("trial_moves_per_s",)} for c in table]}
     return out
 
 
@@ -349,7 +349,9 @@ def time_e2e(args, form, rank, steps, xy0):
     xy = pinned.numpy()
     xy[:] = xy0
     S = args.sweeps_per_step
-    sysg.run(1, S, False)  # capture the step's graph before timing
+    for _ in range(2):  # capture the step graphs of both buffer parities (hd_set_positions swaps them) untimed
+        sysg.set_positions(xy)
+        sysg.run(1, S, False)
     torch.cuda.synchronize()
     att0 = int(sysg.stats()[0][0])
     t0 = time.perf_counter()
@@ -643,6 +645,7 @@ def run_ours(args):
                    "N": args.N, "eta": args.eta, "sweeps_per_step": args.sweeps_per_step, "cells_per_side": geo["m"],
                    "trials_per_cell": geo["trials_per_cell"], "cell_side": geo["w"],
                    "acceptance": main["acceptance"], "l2": "flushed before each timed step (256 MB write)",
+                   "graph_branches": geo["graph_branches"],
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
         "gpu_launches": main["launches"],

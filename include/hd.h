@@ -93,6 +93,28 @@ typedef struct hd_opts {
                                 (>= 2 sigma), e.g. chosen per state point by an
                                 autotuner; NULL: cell_min for every replica [NULL].
                                 Read during hd_init / hd_batch_init only.       */
+    int32_t strips;          /* graph wavefront of the steps hd_run captures, one
+                                replica, HD_SWEEP_SPLIT, threads_per_cell 1: the
+                                cell grid as K strips of two-cell-row bands, each
+                                strip's rebuild and colour passes on its own graph
+                                branch, a strip's phase waiting only for the
+                                previous phase in itself and the two next to it
+                                (in the checkerboard of Sec. II.B a pass reads
+                                one cell row beyond its own cells and a rebuild
+                                moves a disk by at most one cell).  Same chain.
+                                0: automatic (16 when the colour pass is 1.5 to
+                                3.5 waves of resident blocks deep, else none);
+                                1: none; 2 .. 64: K strips (at most m / 2, and
+                                only for one replica, the split kernels and one
+                                thread per cell; else HD_ERR_ARG) [0]          */
+    int32_t replica_branches; /* the steps hd_run captures for 2 .. 64 replicas
+                                (HD_SWEEP_SPLIT, threads_per_cell 1) run each
+                                replica's sweeps on its own graph branch with
+                                one-replica launches, the replicas' chains
+                                concurrently (independent chains, Sec. IV.A's
+                                scan); the measurement stays one batched launch.
+                                Same chains.  0: automatic (on where it applies);
+                                1: off [0]                                      */
 } hd_opts;
 
 enum { HD_SWEEP_SPLIT = 0, HD_SWEEP_FUSED = 1, HD_SWEEP_TMA = 2, HD_SWEEP_PERSISTENT = 3 };
@@ -105,7 +127,9 @@ typedef struct hd_geometry {
     int32_t trials_per_cell;
     int32_t precision;
     int32_t hist_bins;  /* K of the contact histogram                             */
-    int32_t reserved;
+    int32_t graph_branches; /* concurrent branches of the sweeps of hd_run's step
+                               graphs: the strips of a one-replica context, the
+                               replicas of a batch with replica branches, else 1 */
     double L;           /* box side in sigma (fixed form: m * W * 2^-24)          */
     double w;           /* cell side in sigma                                     */
     double delta;       /* maximum displacement per axis in sigma (realised)      */
@@ -237,9 +261,14 @@ int32_t hd_replicas(const hd_ctx *ctx);
  * device to a series (no host synchronisation).  measure == 2 also keeps the
  * local psi_j field of each measurement (Eq. 8) on the device, for
  * hd_psi6_local_device.  Each distinct step is captured once as a CUDA graph
- * and replayed; while profiling is enabled the graph carries a timing event
- * before and after every kernel, and each replay is followed by a
- * synchronisation that adds the kernels' times to hd_kernel_times.
+ * and replayed, its sweeps on concurrent branches where hd_opts asks for strips
+ * or replica branches (graph_branches of hd_get_geometry); while profiling is
+ * enabled the graph instead runs every kernel in order, with a timing event
+ * before and after it, and each replay is followed by a synchronisation that
+ * adds the kernels' times to hd_kernel_times.  Capturing and instantiating a
+ * step graph is a one-time cost per distinct step (at N = 2^20 about 6 ms
+ * serial, about 0.13 s as 16 strips, whose graph holds ~8000 kernel nodes per
+ * 100 sweeps).
  * Asynchronous on the context stream (unless profiling).  R <= 1024.
  * Errors: HD_ERR_ARG for negative counts, an empty step or measure outside
  * 0..2; HD_ERR_REACH as hd_pressure when measuring.

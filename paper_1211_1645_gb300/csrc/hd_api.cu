@@ -36,6 +36,9 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kFx = 16777216.0;  // 2^24 fixed-point units per sigma
 constexpr int kMaxBins = 512;
 constexpr size_t kCellPad = 64;  // elements of padding after every per-generation cell array
+constexpr int kMaxStrips = 64;    // strips of a one-replica graph wavefront
+constexpr int kAutoStrips = 16;   // strips chosen when the colour pass is 1.5 to 3.5 waves deep
+constexpr int kMaxBranches = 64;  // replicas on concurrent branches of a captured step
 
 struct Plan {
     Rep rep;
@@ -135,6 +138,14 @@ struct hd_ctx {
     size_t gev_used = 0;
     StepGraph* prof_capture = nullptr;    // the profiled graph being captured
     cudaStream_t capture_stream = nullptr;
+    // Captured steps run their sweeps on concurrent graph branches: K strips of
+    // bands of a one-replica context (strips > 1), or one branch per replica
+    // (branches).  side: their streams; side_ev: the fork event, one join
+    // event per branch, then the strips' phase events (two sets by parity).
+    int strips = 1;
+    bool branches = false;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;
     double* series = nullptr;       // [cap][R][4]: beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6
     int64_t* series_len = nullptr;  // device counter of recorded steps
     int64_t series_cap = 0;
@@ -387,6 +398,8 @@ void free_ctx(hd_ctx* ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    for (cudaStream_t b : ctx->side) cudaStreamDestroy(b);
+    for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
     if (ctx->series) cudaFree(ctx->series);
     if (ctx->acf) cudaFree(ctx->acf);
     if (ctx->tau) cudaFree(ctx->tau);
@@ -445,10 +458,151 @@ cudaError_t launch(hd_ctx* ctx, int cls, F&& f, bool capturing = false) {
     return e;
 }
 
+// Streams and events of the concurrent branches of captured steps: n
+// branches, and (strips) two sets of n phase events.
+cudaError_t ensure_side(hd_ctx* ctx, int n, bool phases) {
+    while (ctx->side.size() < size_t(n)) {
+        cudaStream_t b = nullptr;
+        const cudaError_t e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        ctx->side.push_back(b);
+    }
+    const size_t need = size_t(1 + n) + (phases ? size_t(2 * n) : 0);
+    while (ctx->side_ev.size() < need) {
+        cudaEvent_t ev = nullptr;
+        const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        ctx->side_ev.push_back(ev);
+    }
+    return cudaSuccess;
+}
+
+// Fork the first n side streams from s (captured: each takes s's current
+// dependencies), and join them back into s.
+cudaError_t fork_side(hd_ctx* ctx, cudaStream_t s, int n) {
+    cudaError_t e = cudaEventRecord(ctx->side_ev[0], s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->side[size_t(i)], ctx->side_ev[0], 0);
+    return e;
+}
+cudaError_t join_side(hd_ctx* ctx, cudaStream_t s, int n) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ctx->side_ev[1 + size_t(i)], ctx->side[size_t(i)]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->side_ev[1 + size_t(i)], 0);
+    }
+    return e;
+}
+
+// Replica branches: the nc sweeps of one draw table, each replica on its own
+// stream with its own one-replica launches (constants as kernel parameters),
+// the replicas' chains running concurrently.  Same chain as the batched
+// launches: the replicas are independent.
+cudaError_t enqueue_replica_branches(hd_ctx* ctx, cudaStream_t s, int nc) {
+    cudaError_t e = fork_side(ctx, s, ctx->R);
+    const int cur0 = ctx->cur;
+    for (int r = 0; r < ctx->R && e == cudaSuccess; ++r) {
+        Rep rep = ctx->reps[size_t(r)];  // this replica alone: its blocks start at 0
+        rep.blk_act = 0;
+        rep.blk_cell = 0;
+        hd::LaunchCfg c = ctx->cfg(ctx->side[size_t(r)]);
+        c.R = 1;
+        c.rep0 = &rep;
+        c.reps = ctx->reps_d + r;
+        c.ntc = (rep.nt == 1 || rep.nt == 2) ? rep.nt : 0;
+        c.blocks_act = int((int64_t(rep.hh) + c.threads - 1) / c.threads);
+        c.blocks_cell = int((int64_t(rep.m) * rep.m + c.threads - 1) / c.threads);
+        const hd::Frame* tab = ctx->table + size_t(r) * (hd::kMaxChunk + 1);
+        unsigned long long* counters = ctx->counters + 2 * size_t(r);
+        int cur = cur0;
+        for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
+            e = launch(ctx, HD_K_REBUILD, [&] {
+                return hd::launch_rebuild(c, tab, j, ctx->buf[cur], ctx->buf[cur ^ 1], ctx->err);
+            }, true);
+            cur ^= 1;
+            for (int p = 0; p < 4 && e == cudaSuccess; ++p)
+                e = launch(ctx, HD_K_PASS, [&] { return hd::launch_pass(c, tab, j, p, ctx->buf[cur], counters); }, true);
+        }
+    }
+    if (e == cudaSuccess) e = join_side(ctx, s, ctx->R);
+    if (nc & 1) ctx->cur ^= 1;
+    return e;
+}
+
+// Graph wavefront of one replica: the nc sweeps of one draw table as K strips
+// of bands (two cell rows each), one stream per strip.  An item of band b
+// reads and writes only cell rows 2b - 1 .. 2b + 2 (a pass reads its cells'
+// eight neighbours, a rebuild moves a disk by at most one cell), so a
+// strip's phase (the rebuild or one colour pass) may start once the previous
+// phase is done in that strip and the two next to it: graph edges, not a
+// global barrier, separate the phases, and the tail of one strip's launch
+// overlaps the next phase of strips that are ready.  Every cell sees the
+// same sequence of phases as in the serial order, so the chain is the same.
+cudaError_t enqueue_strips(hd_ctx* ctx, cudaStream_t s, int nc) {
+    const int K = ctx->strips;
+    const Rep& rep = ctx->reps[0];
+    std::vector<uint32_t> b(size_t(K) + 1);
+    for (int i = 0; i <= K; ++i) b[size_t(i)] = uint32_t((int64_t(rep.hm) * i) / K);
+    cudaError_t e = fork_side(ctx, s, K);
+    const size_t ev_phase = size_t(1 + K);
+    int cur = ctx->cur;
+    int k = 0;  // phase index over the chunk
+    for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
+        for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph, ++k) {
+            const size_t now = ev_phase + size_t(k & 1) * size_t(K), prev = ev_phase + size_t((k & 1) ^ 1) * size_t(K);
+            for (int i = 0; i < K && e == cudaSuccess; ++i) {
+                cudaStream_t bs = ctx->side[size_t(i)];
+                if (k > 0) {  // the previous phase in the two neighbouring strips (its own: stream order)
+                    const int l = (i + K - 1) % K, r = (i + 1) % K;
+                    if (l != i) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(l)], 0);
+                    if (e == cudaSuccess && r != i && r != l) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(r)], 0);
+                    if (e != cudaSuccess) break;
+                }
+                hd::LaunchCfg c = ctx->cfg(bs);
+                const uint32_t lo = b[size_t(i)] * uint32_t(rep.hm), hi = b[size_t(i) + 1] * uint32_t(rep.hm);
+                if (ph == 0) {
+                    c.band_lo = lo;
+                    c.band_span = hi - lo;
+                    e = launch(ctx, HD_K_REBUILD, [&] {
+                        return hd::launch_rebuild(c, ctx->table, j, ctx->buf[cur], ctx->buf[cur ^ 1], ctx->err);
+                    }, true);
+                } else {
+                    c.act_lo = lo;
+                    c.act_hi = hi;
+                    e = launch(ctx, HD_K_PASS, [&] {
+                        return hd::launch_pass(c, ctx->table, j, ph - 1, ctx->buf[cur], ctx->counters);
+                    }, true);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(ctx->side_ev[now + size_t(i)], bs);
+            }
+            if (ph == 0) cur ^= 1;
+        }
+    }
+    if (e == cudaSuccess) e = join_side(ctx, s, K);
+    ctx->cur = cur;
+    return e;
+}
+
 // Enqueue n sweeps on stream s (draw tables of up to kMaxChunk sweeps, then
 // per sweep either one fused launch or a rebuild and four colour passes).
+// While a step graph is captured (not for a profiled graph, whose event nodes
+// time each kernel in order), the sweeps of a one-replica context with strips
+// run as a graph wavefront, and those of a batch with replica branches as
+// one branch per replica.
 cudaError_t enqueue_sweeps(hd_ctx* ctx, cudaStream_t s, int64_t n, bool capturing) {
     const hd::LaunchCfg c = ctx->cfg(s);
+    const bool wave = capturing && !ctx->prof_capture && (ctx->strips > 1 || ctx->branches);
+    if (wave) {
+        const int nb = ctx->strips > 1 ? ctx->strips : ctx->R;
+        cudaError_t e = ensure_side(ctx, nb, ctx->strips > 1);
+        for (int64_t left = n; left > 0 && e == cudaSuccess;) {
+            const int nc = int(std::min<int64_t>(left, hd::kMaxChunk));
+            e = launch(ctx, HD_K_DRAWS, [&] { return hd::launch_draws(c, ctx->table, ctx->frame, ctx->sweep_ctr, nc); },
+                       capturing);
+            if (e == cudaSuccess) e = ctx->strips > 1 ? enqueue_strips(ctx, s, nc) : enqueue_replica_branches(ctx, s, nc);
+            left -= nc;
+        }
+        return e;
+    }
     int64_t left = n;
     cudaError_t e = cudaSuccess;
     while (left > 0 && e == cudaSuccess) {
@@ -542,6 +696,8 @@ void hd_default_opts(hd_opts* o) {
     o->sweep_kernel = HD_SWEEP_SPLIT;
     o->threads_per_cell = 1;
     o->cell_min_per_replica = nullptr;
+    o->strips = 0;
+    o->replica_branches = 0;
 }
 
 const char* hd_status_string(hd_status s) {
@@ -576,6 +732,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         o.sweep_kernel = opts_in->sweep_kernel;
         if (opts_in->threads_per_cell > 0) o.threads_per_cell = opts_in->threads_per_cell;
         o.cell_min_per_replica = opts_in->cell_min_per_replica;
+        o.strips = opts_in->strips;
+        o.replica_branches = opts_in->replica_branches;
     }
     if (o.precision != HD_FP64 && o.precision != HD_FIXED32) return HD_ERR_ARG;
     if (o.lattice != HD_LATTICE_SQUARE && o.lattice != HD_LATTICE_TRIANGULAR) return HD_ERR_ARG;
@@ -589,6 +747,10 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         if (g != 1 && g != 2 && g != 4 && g != 8) return HD_ERR_ARG;
         if (g > 1 && (o.sweep_kernel != HD_SWEEP_SPLIT || o.block_threads * g > 512)) return HD_ERR_ARG;
     }
+    // graph branches: strips only for one replica on the split one-thread pass
+    const bool split1 = o.sweep_kernel == HD_SWEEP_SPLIT && o.threads_per_cell == 1;
+    if (o.strips < 0 || o.strips > kMaxStrips || (o.strips >= 2 && (R != 1 || !split1))) return HD_ERR_ARG;
+    if (o.replica_branches != 0 && o.replica_branches != 1) return HD_ERR_ARG;
 
     std::vector<Plan> plans(static_cast<size_t>(R));
     int cap = 4;
@@ -599,6 +761,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         cap = std::max(cap, plans[size_t(r)].cap);
     }
     cap = cap <= 4 ? 4 : 9;
+    if (o.strips > plans[0].rep.hm) return HD_ERR_ARG;  // every strip at least one band
 
     hd_ctx* ctx = new (std::nothrow) hd_ctx();
     if (!ctx) return HD_ERR_ARG;
@@ -747,6 +910,25 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         ok = ok && dev_alloc(ctx, &ctx->persist_sync, hd::persist_sync_words(ctx->bands));
         ok = ok && hd::persist_grid(ctx->cfg(), &ctx->persist_blocks) == cudaSuccess && ctx->persist_blocks > 0;
     }
+    // Concurrent branches of captured steps.  One replica: K strips when
+    // asked, or automatically 16 when its colour pass is 1.5 to 3.5 waves of
+    // resident blocks deep (measured on GB300 at N = 2^18 .. 2^22: there the
+    // launch tails are a large share of a pass; shallower passes lose more to
+    // the extra graph nodes than the overlap gains, deeper ones have little
+    // tail to hide).  Several replicas: one branch each, up to kMaxBranches.
+    if (ok && R == 1 && split1) {
+        if (o.strips >= 2) {
+            ctx->strips = o.strips;
+        } else if (o.strips == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            ok = cudaGetDevice(&dev) == cudaSuccess &&
+                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                 hd::pass_blocks_per_sm(ctx->cfg(), &per_sm) == cudaSuccess;
+            const double waves = (sms > 0 && per_sm > 0) ? double(ctx->blocks_act) / (double(sms) * per_sm) : 0.0;
+            if (ok && waves >= 1.5 && waves < 3.5 && ctx->reps[0].hm >= 2 * kAutoStrips) ctx->strips = kAutoStrips;
+        }
+    }
+    ctx->branches = R > 1 && R <= kMaxBranches && split1 && o.replica_branches == 0;
     if (!ok) {
         free_ctx(ctx);
         return HD_ERR_CUDA;
@@ -974,7 +1156,7 @@ hd_status hd_get_geometry(hd_ctx* ctx, int32_t r, hd_geometry* g) {
     g->trials_per_cell = rep.nt;
     g->precision = ctx->fixed ? HD_FIXED32 : HD_FP64;
     g->hist_bins = ctx->K;
-    g->reserved = 0;
+    g->graph_branches = ctx->strips > 1 ? ctx->strips : (ctx->branches ? ctx->R : 1);
     g->L = ctx->fixed ? double(rep.LF) / kFx : rep.L;
     g->w = ctx->fixed ? double(rep.W) / kFx : rep.w;
     g->delta = ctx->fixed ? double(rep.D) / kFx : rep.delta;

@@ -37,6 +37,12 @@ struct LaunchCfg {
     int blocks_seg;    // half-row segment grid size of one colour pass (all replicas)
     int persist_blocks;  // grid of the persistent sweep (resident blocks), from persist_grid
     bool persist_stall;  // test hook: the persistent sweep withholds one item and gives up waiting early
+    // One strip of a one-replica sweep (graph wavefront): a colour pass over
+    // the active cells [act_lo, act_hi) of its plane, a rebuild over the
+    // entries band_lo .. band_lo + band_span - 1 of each colour plane.  The
+    // defaults (0, ~0u, 0, 0) cover every cell.
+    uint32_t act_lo = 0u, act_hi = ~0u;
+    uint32_t band_lo = 0u, band_span = 0u;
     cudaStream_t stream;
 };
 
@@ -66,6 +72,9 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t* sweep_ctr, int nchunk);
 cudaError_t launch_rebuild(const LaunchCfg& c, const Frame* table, int j, CellBufs from, CellBufs to,
                            int* err);
+// Resident blocks per SM of the split colour pass of one replica (the
+// occupancy the pass runs at, for sizing the graph wavefront's strips).
+cudaError_t pass_blocks_per_sm(const LaunchCfg& c, int* blocks);
 cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, CellBufs cells,
                         unsigned long long* counters);
 // The colour pass with tpc > 1 threads per active cell (blocks of threads x tpc).

@@ -89,17 +89,29 @@ __global__ void k_draws(const Rep* __restrict__ reps, int R, Frame* __restrict__
 template <bool FIX, int CAP, bool ONE>
 __global__ void __launch_bounds__(256)
 k_rebuild(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const Rep rep1,
-          const Frame* __restrict__ table, int j,
+          const Frame* __restrict__ table, int j, uint32_t x_lo, uint32_t x_span,
           uint8_t* __restrict__ cnt_o, const P2<FIX>* __restrict__ pos_o, const int32_t* __restrict__ pid_o,
           uint8_t* __restrict__ cnt_n, P2<FIX>* __restrict__ pos_n, int32_t* __restrict__ pid_n,
           int* __restrict__ err) {
     pdl_begin();
     const int r = ONE ? 0 : int(rep_of[blockIdx.x]);
     const Rep rep = ONE ? rep1 : reps[r];
-    const uint32_t mm = uint32_t(rep.m) * uint32_t(rep.m);
-    const uint32_t a0 = uint32_t(blockIdx.x - rep.blk_cell) * (2u * blockDim.x) + threadIdx.x;
-    const uint32_t a[2] = {a0, a0 + blockDim.x};
-    const bool live[2] = {a[0] < mm, a[1] < mm};
+    uint32_t a[2];
+    bool live[2];
+    if (ONE && x_span != 0u) {
+        // one strip: entries x_lo + x of colour planes 2y and 2y + 1
+        const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+        a[0] = 2u * blockIdx.y * uint32_t(rep.hh) + x_lo + x;
+        a[1] = a[0] + uint32_t(rep.hh);
+        live[0] = live[1] = x < x_span;
+    } else {
+        const uint32_t mm = uint32_t(rep.m) * uint32_t(rep.m);
+        const uint32_t a0 = uint32_t(blockIdx.x - rep.blk_cell) * (2u * blockDim.x) + threadIdx.x;
+        a[0] = a0;
+        a[1] = a0 + blockDim.x;
+        live[0] = a[0] < mm;
+        live[1] = a[1] < mm;
+    }
     if (rebuild_pair<FIX, CAP, false>(rep, table + size_t(r) * (kMaxChunk + 1), j, a, live, cnt_o, pos_o, pid_o,
                                       cnt_n, pos_n, pid_n))
         atomicOr(err, 1);
@@ -119,7 +131,7 @@ k_rebuild(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, con
 template <bool FIX, int CAP, int NTC, bool ONE>
 __global__ void __launch_bounds__(256)
 k_pass(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const Rep rep1,
-       const Frame* __restrict__ table, int j, int p,
+       const Frame* __restrict__ table, int j, int p, uint32_t a_lo, uint32_t a_hi,
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
     pdl_begin();
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -128,11 +140,11 @@ k_pass(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const 
     int32_t* s_crowd_id = reinterpret_cast<int32_t*>(s_crowd + size_t(blockDim.x) * CAP);
     const int r = ONE ? 0 : int(rep_of[blockIdx.x]);
     const Rep rep = ONE ? rep1 : reps[r];
-    const uint32_t a = uint32_t(blockIdx.x - rep.blk_act) * blockDim.x + threadIdx.x;
+    const uint32_t a = a_lo + uint32_t(blockIdx.x - rep.blk_act) * blockDim.x + threadIdx.x;
     const Frame f = table[size_t(r) * (kMaxChunk + 1) + j];
     const int col = int(f.perm >> (2 * p)) & 3;
     uint32_t att = 0, acc = 0;
-    if (a < uint32_t(rep.hh)) {
+    if (a < a_hi && a < uint32_t(rep.hh)) {
         pass_cell<FIX, CAP, NTC, false>(rep, f, col, a, cnt, pos, pid, s_nbr + threadIdx.x * kNbrStride,
                                         s_crowd + threadIdx.x * CAP, s_crowd_id + threadIdx.x * CAP, att, acc);
     }
@@ -189,13 +201,18 @@ cudaError_t launch_draws(const LaunchCfg& c, Frame* table, Frame* cur, uint64_t*
 template <bool FIX, int CAP>
 static cudaError_t rebuild_t(const LaunchCfg& c, const Frame* table, int j, CellBufs a, CellBufs b, int* err) {
     // one replica: blocks of `threads` threads over 2 threads cells each (no
-    // per-replica block partition to follow; 1% faster than half-size blocks)
-    if (c.R == 1)
-        return launch_k(k_rebuild<FIX, CAP, true>, dim3((c.blocks_cell + 1) / 2), dim3(c.threads), 0, c.stream, c.reps,
-                        c.rep_of_cell, *c.rep0, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
+    // per-replica block partition to follow; 1% faster than half-size blocks);
+    // one strip: a thread per planar entry of the band range, its cells in two
+    // colour planes (grid y picks the pair)
+    if (c.R == 1) {
+        const dim3 grid = c.band_span ? dim3((c.band_span + uint32_t(c.threads) - 1) / uint32_t(c.threads), 2)
+                                      : dim3((c.blocks_cell + 1) / 2);
+        return launch_k(k_rebuild<FIX, CAP, true>, grid, dim3(c.threads), 0, c.stream, c.reps, c.rep_of_cell, *c.rep0,
+                        table, j, c.band_lo, c.band_span, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
                         (P2<FIX>*)b.pos, b.pid, err);
+    }
     return launch_k(k_rebuild<FIX, CAP, false>, dim3(c.blocks_cell), dim3(c.threads / 2), 0, c.stream, c.reps,
-                    c.rep_of_cell, Rep{}, table, j, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
+                    c.rep_of_cell, Rep{}, table, j, 0u, 0u, a.cnt, (const P2<FIX>*)a.pos, (const int32_t*)a.pid, b.cnt,
                     (P2<FIX>*)b.pos, b.pid, err);
 }
 
@@ -215,13 +232,17 @@ static cudaError_t pass_t(const LaunchCfg& c, const Frame* table, int j, int p, 
         cudaFuncSetAttribute(k_pass<FIX, CAP, NTC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(pass_smem<FIX, CAP>(256)));
     });
-    if (c.R == 1)
-        return launch_k(k_pass<FIX, CAP, NTC, true>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps,
-                        c.rep_of_act, *c.rep0, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid,
-                        counters);
+    if (c.R == 1) {
+        // a strip covers its active-cell range; the whole plane otherwise
+        const int blocks = c.act_hi != ~0u ? int((c.act_hi - c.act_lo + uint32_t(c.threads) - 1) / uint32_t(c.threads))
+                                          : c.blocks_act;
+        return launch_k(k_pass<FIX, CAP, NTC, true>, dim3(blocks), dim3(c.threads), smem, c.stream, c.reps,
+                        c.rep_of_act, *c.rep0, table, j, p, c.act_lo, c.act_hi, (const uint8_t*)cells.cnt,
+                        (P2<FIX>*)cells.pos, cells.pid, counters);
+    }
     return launch_k(k_pass<FIX, CAP, NTC, false>, dim3(c.blocks_act), dim3(c.threads), smem, c.stream, c.reps,
-                    c.rep_of_act, Rep{}, table, j, p, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos, cells.pid,
-                    counters);
+                    c.rep_of_act, Rep{}, table, j, p, 0u, ~0u, (const uint8_t*)cells.cnt, (P2<FIX>*)cells.pos,
+                    cells.pid, counters);
 }
 
 template <bool FIX, int CAP>
@@ -237,6 +258,22 @@ cudaError_t launch_pass(const LaunchCfg& c, const Frame* table, int j, int p, Ce
     if (c.tpc > 1) return launch_pass_group(c, table, j, p, cells, counters);
     if (c.fixed) return c.cap == 4 ? pass_nt<true, 4>(c, table, j, p, cells, counters) : pass_nt<true, 9>(c, table, j, p, cells, counters);
     return c.cap == 4 ? pass_nt<false, 4>(c, table, j, p, cells, counters) : pass_nt<false, 9>(c, table, j, p, cells, counters);
+}
+
+// Resident blocks per SM of the one-replica colour pass (split kernel).
+template <bool FIX, int CAP, int NTC>
+static cudaError_t pass_occupancy_t(const LaunchCfg& c, int* blocks) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_pass<FIX, CAP, NTC, true>, c.threads,
+                                                         pass_smem<FIX, CAP>(c.threads));
+}
+
+cudaError_t pass_blocks_per_sm(const LaunchCfg& c, int* blocks) {
+    if (c.fixed) {
+        if (c.cap == 4) return c.ntc == 1 ? pass_occupancy_t<true, 4, 1>(c, blocks) : pass_occupancy_t<true, 4, 0>(c, blocks);
+        return c.ntc == 1 ? pass_occupancy_t<true, 9, 1>(c, blocks) : pass_occupancy_t<true, 9, 0>(c, blocks);
+    }
+    if (c.cap == 4) return c.ntc == 1 ? pass_occupancy_t<false, 4, 1>(c, blocks) : pass_occupancy_t<false, 4, 0>(c, blocks);
+    return c.ntc == 1 ? pass_occupancy_t<false, 9, 1>(c, blocks) : pass_occupancy_t<false, 9, 0>(c, blocks);
 }
 
 template <bool FIX, int CAP>

@@ -40,6 +40,8 @@ class hd_opts(ctypes.Structure):
         ("sweep_kernel", ctypes.c_int32),
         ("threads_per_cell", ctypes.c_int32),
         ("cell_min_per_replica", ctypes.c_void_p),
+        ("strips", ctypes.c_int32),
+        ("replica_branches", ctypes.c_int32),
     ]
 
 
@@ -51,7 +53,7 @@ class hd_geometry(ctypes.Structure):
         ("trials_per_cell", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("hist_bins", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("graph_branches", ctypes.c_int32),
         ("L", ctypes.c_double),
         ("w", ctypes.c_double),
         ("delta", ctypes.c_double),
@@ -151,10 +153,13 @@ SWEEP_KERNELS = {"split": 0, "fused": 1, "tma": 2, "persistent": 3}
 
 
 def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=50, hist_dr=1e-3,
-              cell_min=2.0, block_threads=128, sweep_kernel="split", threads_per_cell=1) -> hd_opts:
+              cell_min=2.0, block_threads=128, sweep_kernel="split", threads_per_cell=1, strips=0,
+              replica_branches=0) -> hd_opts:
     """hd_opts from keyword values.  cell_min may be one value or one per
     replica (a sequence); the per-replica array is kept alive on the returned
-    struct until it is dropped (the library reads it only at creation)."""
+    struct until it is dropped (the library reads it only at creation).
+    strips: 0 automatic, 1 none, K >= 2 strips; replica_branches: 0
+    automatic, 1 off (see hd.h)."""
     o = hd_default_opts()
     o.precision = PRECISIONS.get(precision, precision)
     o.lattice = LATTICES.get(lattice, lattice)
@@ -171,6 +176,8 @@ def make_opts(precision="fp64", lattice="square", trials_per_cell=0, hist_bins=5
     o.block_threads = int(block_threads)
     o.sweep_kernel = SWEEP_KERNELS.get(sweep_kernel, sweep_kernel)
     o.threads_per_cell = int(threads_per_cell)
+    o.strips = int(strips)
+    o.replica_branches = int(replica_branches)
     return o
 
 
@@ -404,9 +411,9 @@ class HardDisks:
 
     def __init__(self, N, eta, delta, seed, sigma=1.0, precision="fp64", lattice="square", trials_per_cell=0,
                  hist_bins=50, hist_dr=1e-3, cell_min=2.0, block_threads=128, sweep_kernel="split",
-                 threads_per_cell=1):
+                 threads_per_cell=1, strips=0, replica_branches=0):
         opts = make_opts(precision, lattice, trials_per_cell, hist_bins, hist_dr, cell_min, block_threads,
-                         sweep_kernel, threads_per_cell)
+                         sweep_kernel, threads_per_cell, strips, replica_branches)
         if np.ndim(N) == 0:
             self.h = hd_init(N, eta, sigma, delta, seed, opts)
         else:

@@ -8,9 +8,10 @@ steps of the library on the current GPU:
 * for one workload (``autotune``): the minimum cell side, the sweep kernel
   (split launches, one fused shared-memory launch per sweep, or one
   persistent launch for many sweeps), the threads
-  per block of the split kernels and the threads per active cell of the
+  per block of the split kernels, the threads per active cell of the
   split colour pass (1, or a group of 2, 4 or 8 lanes that split the overlap
-  tests and combine them with a warp ballot);
+  tests and combine them with a warp ballot), and for the split one-thread
+  pass the strips of the step graph's wavefront (hd_opts.strips);
 * for a batch of replicas at different state points, such as the
   equation-of-state scan of Sec. IV.A (``autotune_replicas``): first each
   replica's own cell side, timed on that replica alone, then the threads per
@@ -52,33 +53,39 @@ def _time(g, sweeps, steps):
 
 
 def time_config(N, eta, delta, seed, precision, cell_min, sweep_kernel, block_threads, sweeps=50, steps=3,
-                threads_per_cell=1):
+                threads_per_cell=1, strips=0):
     """Attempted trial moves per second of `steps` graph-captured steps of
     `sweeps` sweeps (after one untimed step), timed with CUDA events.  N, eta,
-    delta, seed and cell_min may be per-replica lists (one batched context)."""
+    delta, seed and cell_min may be per-replica lists (one batched context).
+    strips: hd_opts.strips (0 automatic, 1 none, K)."""
     g = HardDisks(N, eta, delta, seed, precision=precision, cell_min=cell_min, sweep_kernel=sweep_kernel,
-                  block_threads=block_threads, threads_per_cell=threads_per_cell)
+                  block_threads=block_threads, threads_per_cell=threads_per_cell, strips=strips)
     rate = _time(g, sweeps, steps)
     geo = g.geometry()
     g.close()
     return {"cell_min": cell_min, "sweep_kernel": sweep_kernel, "block_threads": block_threads,
-            "threads_per_cell": threads_per_cell, "cells_per_side": geo["m"],
-            "trials_per_cell": geo["trials_per_cell"], "trial_moves_per_s": rate}
+            "threads_per_cell": threads_per_cell, "strips": strips, "graph_branches": geo["graph_branches"],
+            "cells_per_side": geo["m"], "trials_per_cell": geo["trials_per_cell"], "trial_moves_per_s": rate}
 
 
 def autotune(N, eta, delta, seed=1, precision="fixed", cell_mins=(2.0, 2.2, 2.4), kernels=("split", "fused"),
-             block_threads=(64, 128, 256), threads_per_cell=(1,), sweeps=50, steps=3):
+             block_threads=(64, 128, 256), threads_per_cell=(1,), strips=(1,), sweeps=50, steps=3):
     """Time every candidate and return (best, all results sorted by speed).
     Candidates whose geometry or launch shape is invalid for the workload are
-    skipped (the library rejects them at creation)."""
+    skipped (the library rejects them at creation).  strips applies to the
+    split kernel with one thread per cell (others run without strips)."""
     results = []
-    for cm, kern, bt, g in itertools.product(cell_mins, kernels, block_threads, threads_per_cell):
+    for cm, kern, bt, g, k in itertools.product(cell_mins, kernels, block_threads, threads_per_cell, strips):
         if kern == "fused" and (bt != block_threads[0] or g != 1):
             continue  # the fused kernel has a fixed block size and one thread per cell
         if kern in ("tma", "persistent") and g != 1:
             continue
+        wave = kern == "split" and g == 1
+        if not wave and k != strips[0]:
+            continue  # strips apply to the split one-thread pass: the others are timed once, without
         try:
-            results.append(time_config(N, eta, delta, seed, precision, cm, kern, bt, sweeps, steps, g))
+            results.append(time_config(N, eta, delta, seed, precision, cm, kern, bt, sweeps, steps, g,
+                                       k if wave else 1))
         except Exception:  # an invalid candidate (e.g. a cell too wide for the box)
             continue
     results.sort(key=lambda r: -r["trial_moves_per_s"])

@@ -48,6 +48,7 @@ def test_status_strings_and_defaults(hdlib):
     assert "argument" in b.status_string(1)
     o = b.hd_default_opts()
     assert (o.precision, o.lattice, o.hist_bins, o.hist_dr, o.cell_min) == (0, 0, 50, 1e-3, 2.0)
+    assert (o.strips, o.replica_branches, o.threads_per_cell) == (0, 0, 1)
 
 
 @pytest.mark.parametrize("N,eta,sigma,delta,kw", [
@@ -66,6 +67,12 @@ def test_status_strings_and_defaults(hdlib):
     (256, 0.7, 1.0, 0.1, {"threads_per_cell": 8}),  # 128 cells x 8 lanes > 512 threads
     (256, 0.7, 1.0, 0.1, {"threads_per_cell": 2, "sweep_kernel": "tma"}),  # groups only in the split pass
     (256, 0.7, 1.0, 0.1, {"cell_min": [1.9]}),     # a per-replica cell side below a diameter
+    (256, 0.7, 1.0, 0.1, {"strips": -1}),          # strips: 0 automatic, 1 none, 2 .. 64
+    (256, 0.7, 1.0, 0.1, {"strips": 65}),
+    (256, 0.7, 1.0, 0.1, {"strips": 9}),           # m = 16: eight bands, fewer than nine strips
+    (256, 0.7, 1.0, 0.1, {"strips": 2, "sweep_kernel": "tma"}),  # strips only on the split kernels
+    (256, 0.7, 1.0, 0.1, {"strips": 2, "threads_per_cell": 2}),  # ... with one thread per cell
+    (256, 0.7, 1.0, 0.1, {"replica_branches": 2}),  # 0 automatic or 1 off
 ])
 def test_invalid_arguments_rejected_on_host(hdlib, N, eta, sigma, delta, kw):
     hd, lib = hdlib
@@ -90,6 +97,20 @@ def test_batch_replica_count_bounds(hdlib):
         st = lib.hd_batch_init(ctypes.byref(h), ctypes.c_int32(R), one_n, one_d, ctypes.c_double(1.0), one_d, one_s,
                                None)
         assert st == b.HD_ERR_ARG and not h.value
+
+
+def test_strips_need_a_single_replica(hdlib):
+    """Strips split one replica's grid; a batch takes replica branches instead."""
+    hd, lib = hdlib
+    from paper_1211_1645_gb300 import hd as b
+    n = (ctypes.c_int64 * 2)(256, 256)
+    d = (ctypes.c_double * 2)(0.7, 0.7)
+    dl = (ctypes.c_double * 2)(0.1, 0.1)
+    sd = (ctypes.c_uint64 * 2)(1, 2)
+    h = ctypes.c_void_p()
+    opts = b.make_opts(strips=2)
+    st = lib.hd_batch_init(ctypes.byref(h), ctypes.c_int32(2), n, d, ctypes.c_double(1.0), dl, sd, ctypes.byref(opts))
+    assert st == b.HD_ERR_ARG and not h.value
 
 
 def test_null_context_calls(hdlib):

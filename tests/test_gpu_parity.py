@@ -541,3 +541,98 @@ def test_psi6_on_the_start_lattice(hd, oracle_mod, form, lattice):
     assert np.array_equal(loc, rloc)
     assert glob[0] == rglob
     g.close()
+
+
+STRIP_CASES = {
+    # N = 4096 at eta = 0.70: m = 66, 33 bands (33 strips: one band each)
+    "N4096": (dict(N=4096, eta=0.70, delta=0.1, seed=71), (2, 3, 5, 33)),
+    # three trials per occupied cell (the run-time trial loop)
+    "three_trials": (dict(N=400, eta=0.60, delta=0.2, seed=72, nt=3), (2, 3)),
+    # capacity-9 cells (m = 14, seven bands)
+    "cap9_cells": (dict(N=300, eta=0.50, delta=0.4, seed=73, cell_min=3.0), (2, 7)),
+}
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+@pytest.mark.parametrize("case", list(STRIP_CASES))
+def test_strip_wavefront(hd, oracle_mod, form, case):
+    """Graph wavefront of one replica (hd_opts.strips = K): each strip's
+    rebuild and colour passes on its own graph branch, ordered only against
+    the two neighbouring strips.  Steps of 7 sweeps (both buffer parities)
+    with a measurement each: series, trial counts and every position against
+    the oracle, for several K including one band per strip."""
+    kw, Ks = STRIP_CASES[case]
+    for K in Ks:
+        g = hd.HardDisks(kw["N"], kw["eta"], kw["delta"], kw["seed"], precision=form, trials_per_cell=kw.get("nt", 0),
+                         cell_min=kw.get("cell_min", 2.0), strips=K)
+        o = oracle_mod.OracleChain(kw["N"], kw["eta"], kw["delta"], kw["seed"], form=form, nt=kw.get("nt", 0),
+                                   cell_min=kw.get("cell_min", 2.0))
+        assert g.geometry()["graph_branches"] == K
+        g.run(3, 7, measure=True)
+        ser = g.series()
+        L = o.geometry()["L"]
+        for k in range(3):
+            o.sweep(7)
+            want = oracle_mod.contact_pressure(o.histogram(50, 1e-3), kw["N"], L, o.realised_dr(1e-3))
+            _, rglob = o.psi6()
+            assert abs(ser[k, 0, 0] - want["betaP_over_rho"]) <= PRESSURE_TOL * max(1.0, abs(want["betaP_over_rho"]))
+            assert complex(ser[k, 0, 2], ser[k, 0, 3]) == rglob
+        assert_same_state(g, o)
+        g.sweep(3)  # the serial path continues the same chain
+        o.sweep(3)
+        assert_same_state(g, o)
+        g.close()
+
+
+def test_strip_wavefront_full_size(hd):
+    """N = 1024^2 at eta = 0.716 (the benchmark system): the automatic choice
+    and an uneven strip count (seven strips of 76 or 77 bands) give the same
+    chain as the serial step graph over two steps of 50 sweeps."""
+    N = 1024 * 1024
+    runs = {}
+    for K in (1, 0, 7):
+        g = hd.HardDisks(N, 0.716, 0.1, 1, precision="fixed", strips=K)
+        gb = g.geometry()["graph_branches"]
+        if K == 1:
+            assert gb == 1
+        elif K == 7:
+            assert gb == 7
+        else:
+            assert gb in (1, 16)  # 16 where the colour pass is 1.5 to 3.5 waves deep
+        g.run(2, 50, measure=True)
+        runs[K] = (g.positions(), g.stats(), g.series())
+        g.close()
+    for K in (0, 7):
+        assert np.array_equal(runs[K][0], runs[1][0])
+        assert np.array_equal(runs[K][1][0], runs[1][1][0]) and np.array_equal(runs[K][1][1], runs[1][1][1])
+        assert np.array_equal(runs[K][2], runs[1][2])
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_replica_branches(hd, oracle_mod, form):
+    """Replicas of uneven N and eta on concurrent graph branches (the
+    default for a batch on the split kernels) against each replica's oracle
+    chain, and the same context with the branches off (one batched launch
+    per phase) giving the same series and positions."""
+    Ns = [16 ** 2, 24 ** 2, 32 ** 2, 20 ** 2, 17 ** 2]
+    etas = [0.700, 0.701, 0.702, 0.703, 0.704]
+    seeds = [111, 112, 113, 114, 115]
+    out = {}
+    for rb in (0, 1):
+        g = hd.HardDisks(Ns, etas, [0.1] * 5, seeds, precision=form, replica_branches=rb)
+        assert g.geometry()["graph_branches"] == (5 if rb == 0 else 1)
+        g.run(3, 9, measure=True)
+        out[rb] = (g.positions(), g.stats(), g.series())
+        g.close()
+    os_ = [oracle_mod.OracleChain(n, e, 0.1, sd, form=form) for n, e, sd in zip(Ns, etas, seeds)]
+    for o in os_:
+        o.sweep(27)
+    xy, (att, acc), ser = out[0]
+    off = 0
+    for r, o in enumerate(os_):
+        assert (int(att[r]), int(acc[r])) == o.stats()
+        assert np.array_equal(xy[off:off + Ns[r]], o.positions())
+        _, rglob = o.psi6()
+        assert complex(ser[-1, r, 2], ser[-1, r, 3]) == rglob
+        off += Ns[r]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])

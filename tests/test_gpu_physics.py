@@ -81,11 +81,14 @@ def test_fixed_vs_fp64_equation_of_state(hd):
 def test_autotuner_picks_a_valid_fast_configuration(hd):
     from paper_1211_1645_gb300.tune import autotune
     best, table = autotune(65536, 0.708, 0.1, cell_mins=(2.0, 2.4), block_threads=(128, 256),
-                           threads_per_cell=(1, 2), sweeps=20, steps=2)
-    assert best is not None and len(table) >= 6
+                           threads_per_cell=(1, 2), strips=(1, 16), sweeps=20, steps=2)
+    assert best is not None and len(table) >= 8
     assert best["trial_moves_per_s"] == max(r["trial_moves_per_s"] for r in table)
     assert best["cell_min"] in (2.0, 2.4) and best["sweep_kernel"] in ("split", "fused")
     assert {r["threads_per_cell"] for r in table} == {1, 2}
+    # strips only on the split one-thread pass, where the step graph then has that many branches
+    assert {(r["strips"], r["graph_branches"]) for r in table if r["sweep_kernel"] == "split"
+            and r["threads_per_cell"] == 1} == {(1, 1), (16, 16)}
 
 
 def test_autotuner_per_replica_choice_runs_the_same_chains(hd, oracle_mod):
