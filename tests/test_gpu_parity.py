@@ -636,3 +636,33 @@ def test_replica_branches(hd, oracle_mod, form):
         assert complex(ser[-1, r, 2], ser[-1, r, 3]) == rglob
         off += Ns[r]
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_wavefront_across_draw_tables(hd, oracle_mod, form):
+    """Steps of 300 sweeps (two draw tables of 256 and 44 sweeps, each forked
+    into branches and joined again) as strips of one replica and as replica
+    branches of a batch, against the oracle."""
+    g = hd.HardDisks(400, 0.70, 0.1, 81, precision=form, strips=3)
+    o = oracle_mod.OracleChain(400, 0.70, 0.1, 81, form=form)
+    g.run(1, 300, measure=True)
+    o.sweep(300)
+    assert_same_state(g, o)
+    _, rglob = o.psi6()
+    ser = g.series()
+    assert complex(ser[0, 0, 2], ser[0, 0, 3]) == rglob
+    g.close()
+    Ns, etas, seeds = [16 ** 2, 20 ** 2], [0.70, 0.71], [82, 83]
+    g = hd.HardDisks(Ns, etas, [0.1] * 2, seeds, precision=form)
+    assert g.geometry()["graph_branches"] == 2
+    os_ = [oracle_mod.OracleChain(n, e, 0.1, sd, form=form) for n, e, sd in zip(Ns, etas, seeds)]
+    g.run(1, 300, measure=False)
+    att, acc = g.stats()
+    xy = g.positions()
+    off = 0
+    for r, o in enumerate(os_):
+        o.sweep(300)
+        assert (int(att[r]), int(acc[r])) == o.stats()
+        assert np.array_equal(xy[off:off + Ns[r]], o.positions())
+        off += Ns[r]
+    g.close()
