@@ -671,9 +671,20 @@ cudaError_t enqueue_psi6(hd_ctx* ctx, cudaStream_t s, bool local, bool capturing
 cudaError_t enqueue_step(hd_ctx* ctx, cudaStream_t s, int sweeps, bool measure, bool local, bool capturing) {
     cudaError_t e = enqueue_sweeps(ctx, s, sweeps, capturing);
     if (e != cudaSuccess || !measure) return e;
-    e = enqueue_pressure(ctx, s, capturing);
-    if (e != cudaSuccess) return e;
-    e = enqueue_psi6(ctx, s, local, capturing);
+    if (capturing && !ctx->prof_capture) {
+        // the histogram and psi_6 only read the cells: in a step graph psi_6
+        // runs on a branch of its own, beside the histogram and the fit
+        // (measured: 3.95 -> 3.93 ms per step at N = 2^20)
+        e = ensure_side(ctx, 1, false);
+        if (e == cudaSuccess) e = fork_side(ctx, s, 1);
+        if (e == cudaSuccess) e = enqueue_psi6(ctx, ctx->side[0], local, capturing);
+        if (e == cudaSuccess) e = enqueue_pressure(ctx, s, capturing);
+        if (e == cudaSuccess) e = join_side(ctx, s, 1);
+    } else {
+        e = enqueue_pressure(ctx, s, capturing);
+        if (e != cudaSuccess) return e;
+        e = enqueue_psi6(ctx, s, local, capturing);
+    }
     if (e != cudaSuccess) return e;
     return hd::launch_record(ctx->cfg(s), ctx->fit, ctx->psi_res, ctx->series, ctx->series_len, ctx->series_cap,
                              ctx->err);
