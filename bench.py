@@ -333,39 +333,46 @@ def time_extras(args, rank, world, dev):
 def time_e2e(args, form, rank, steps, xy0):
     """Same metric through the public API with host buffers: each step uploads
     the step's input configuration from pinned host memory (hd_set_positions:
-    copy and binning on the device), runs the sweeps (hd_run, one graph
-    launch) and reads the step's result back (the contact pressure and
-    Psi_6, hd_pressure and hd_psi6).  The input is xy0, the configuration the
-    device-timed leg ended in, so that both legs time the same state (trial
-    moves per sweep are the occupied cells, which a fresh lattice has more
-    of than a relaxed configuration)."""
-    import numpy as np
+    copy and binning on the device), runs the step (hd_run: one graph launch
+    of the sweeps and the device-side pressure and Psi_6 measurement) and
+    reads the step's result back (hd_series: the recorded count, then the
+    step's beta P / rho, g(2 sigma+) and Psi_6; the series is then cleared).
+    The input is xy0, the configuration the device-timed leg ended in, so
+    that both legs time the same state (trial moves per sweep are the
+    occupied cells, which a fresh lattice has more of than a relaxed
+    configuration)."""
     import torch
 
     import paper_1211_1645_gb300 as hd
 
-    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form, cell_min=args.cell_min)
+    sysg = hd.HardDisks(args.N, args.eta, args.delta, args.seed + rank, precision=form, cell_min=args.cell_min,
+                        strips=args.strips)
     pinned = torch.empty((xy0.shape[0], 2), dtype=torch.float64, pin_memory=True)
     xy = pinned.numpy()
     xy[:] = xy0
     S = args.sweeps_per_step
-    for _ in range(2):  # capture the step graphs of both buffer parities (hd_set_positions swaps them) untimed
+    sysg.series_reserve(4)
+
+    def step():
         sysg.set_positions(xy)
-        sysg.run(1, S, False)
+        sysg.run(1, S, True)
+        result = sysg.series()[-1]
+        sysg.series_clear()
+        return result
+
+    for _ in range(2):  # capture the step graphs of both buffer parities (hd_set_positions swaps them) untimed
+        step()
     torch.cuda.synchronize()
     att0 = int(sysg.stats()[0][0])
     t0 = time.perf_counter()
     for _ in range(steps):
-        sysg.set_positions(xy)
-        sysg.run(1, S, False)
-        sysg.pressure(want_hist=False)
-        sysg.psi6(want_local=False)
+        step()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     attempts = int(sysg.stats()[0][0]) - att0
     sysg.close()
     return {"value": attempts / dt, "unit": UNIT, "h2d_bytes_per_step": int(xy.nbytes),
-            "d2h_bytes_per_step": 8 * 4 + 4 * 2, "input": "the device-timed leg's final configuration, every step"}
+            "d2h_bytes_per_step": 8 + 8 + 4 * 8, "input": "the device-timed leg's final configuration, every step"}
 
 
 def algorithmic_bytes(kernel, N, m, form):
