@@ -940,6 +940,10 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
         }
     }
     ctx->branches = R > 1 && R <= kMaxBranches && split1 && o.replica_branches == 0;
+    // the branches' streams and events exist before any step is captured
+    // (one side stream at least: the measurement's psi_6 branch)
+    ok = ok && ensure_side(ctx, std::max(1, ctx->strips > 1 ? ctx->strips : (ctx->branches ? R : 1)),
+                           ctx->strips > 1) == cudaSuccess;
     if (!ok) {
         free_ctx(ctx);
         return HD_ERR_CUDA;
