@@ -225,17 +225,27 @@ def test_table2_psi6_correlation_time(hd):
     g.close()
 
 
+@pytest.mark.parametrize("layout", ["one", "strips", "branches"])
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
-def test_set_delta_reaches_captured_steps(hd, form):
-    """A single replica's constants enter the sweep launches by value, so a
-    changed delta must reach the graph-captured steps too: graph steps with
-    a delta change in between equal direct sweeps with the same change."""
-    a = hd.HardDisks(1000, 0.65, 0.1, 6, precision=form)
-    b = hd.HardDisks(1000, 0.65, 0.1, 6, precision=form)
+def test_set_delta_reaches_captured_steps(hd, form, layout):
+    """One-replica launches (a single replica, its strips, or each replica's
+    branch of a batch) take the replica's constants by value, so a changed
+    delta must reach the graph-captured steps too: graph steps with a delta
+    change in between equal direct sweeps with the same change."""
+    if layout == "branches":
+        args = ([1000, 576, 784], [0.65, 0.66, 0.64], [0.1] * 3, [6, 7, 8])
+        new_delta = [0.25, 0.2, 0.15]
+    else:
+        args = (1000, 0.65, 0.1, 6)
+        new_delta = 0.25
+    kw = {"strips": 3} if layout == "strips" else {}
+    a = hd.HardDisks(*args, precision=form, **kw)
+    b = hd.HardDisks(*args, precision=form)
+    assert a.geometry()["graph_branches"] == {"one": 1, "strips": 3, "branches": 3}[layout]
     a.run(1, 7, False)
     b.sweep(7)
-    a.set_delta(0.25)
-    b.set_delta(0.25)
+    a.set_delta(new_delta)
+    b.set_delta(new_delta)
     a.run(2, 7, False)
     b.sweep(14)
     assert np.array_equal(a.positions(), b.positions())
