@@ -144,6 +144,9 @@ struct hd_ctx {
     // event per branch, then the strips' phase events (two sets by parity).
     int strips = 1;
     bool branches = false;
+    // host-pinned scratch: a count and the device error word, read back
+    // together with one synchronisation
+    int64_t* pinned = nullptr;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_ev;
     double* series = nullptr;       // [cap][R][4]: beta P / rho, g(2 sigma+), Re Psi_6, Im Psi_6
@@ -368,10 +371,9 @@ hd_status upload_cells(hd_ctx* ctx, const HostCells& h) {
 
 // Read the device error flag after a synchronisation.  Overflow is sticky
 // (disks were dropped); a measurement reach failure is reported once.
-hd_status check_flags(hd_ctx* ctx) {
-    int flag = 0;
-    HD_CK(ctx, cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+// The status a value of the device error word stands for (the sticky ones
+// made sticky; a reach error cleared on the device).
+hd_status flags_status(hd_ctx* ctx, int flag) {
     if (flag & 1) {
         ctx->sticky = HD_ERR_OVERFLOW;
         return HD_ERR_OVERFLOW;
@@ -388,6 +390,14 @@ hd_status check_flags(hd_ctx* ctx) {
     return HD_OK;
 }
 
+// Wait for the context's stream and report its device error word.
+hd_status check_flags(hd_ctx* ctx) {
+    int flag = 0;
+    HD_CK(ctx, cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return flags_status(ctx, flag);
+}
+
 void drop_graphs(hd_ctx* ctx) {
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
@@ -399,6 +409,7 @@ void free_ctx(hd_ctx* ctx) {
     drop_graphs(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (cudaStream_t b : ctx->side) cudaStreamDestroy(b);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
     if (ctx->series) cudaFree(ctx->series);
     if (ctx->acf) cudaFree(ctx->acf);
@@ -910,6 +921,7 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     ok = ok && dev_alloc(ctx, &ctx->rep_of_act, size_t(ctx->blocks_act));
     ok = ok && dev_alloc(ctx, &ctx->rep_of_cell, size_t(ctx->blocks_cell));
     ok = ok && dev_alloc(ctx, &ctx->xy, size_t(2 * ctx->Ntot));
+    ok = ok && cudaMallocHost(reinterpret_cast<void**>(&ctx->pinned), 2 * sizeof(int64_t)) == cudaSuccess;
     ctx->bands = band0;
     if (ctx->persist) {
         // Test hook for the persistent sweep's bounded waits: with the
@@ -1141,11 +1153,11 @@ hd_status hd_set_positions(hd_ctx* ctx, const double* xy) {
         return (bad & hd::kErrBinInput) ? HD_ERR_ARG : HD_ERR_OVERFLOW;
     }
     ctx->cur ^= 1;
-    // the generation left behind must be cleared for the next rebuild; the frame is unshifted
+    // the generation left behind must be cleared for the next rebuild; the
+    // frame is unshifted (stream-ordered before any later work: no wait)
     HD_CK(ctx, cudaMemsetAsync(ctx->buf[ctx->cur ^ 1].cnt, 0, cnt_bytes, ctx->stream));
     HD_CK(ctx, cudaMemsetAsync(ctx->frame, 0, sizeof(Frame) * size_t(ctx->R), ctx->stream));
-    HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
-    return check_flags(ctx);
+    return flags_status(ctx, flag);  // the word as read after the binning, which follows all earlier work
 }
 
 hd_status hd_stats(hd_ctx* ctx, uint64_t* attempts, uint64_t* accepts) {
@@ -1289,10 +1301,12 @@ hd_status hd_series(hd_ctx* ctx, int64_t* n_steps, double* out, int64_t max_step
     if (ctx->sticky != HD_OK) return HD_ERR_STATE;
     *n_steps = 0;
     if (!ctx->series) return HD_OK;
-    int64_t len = 0;
-    HD_CK(ctx, cudaMemcpyAsync(&len, ctx->series_len, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    // the count and the error word with one wait
+    HD_CK(ctx, cudaMemcpyAsync(&ctx->pinned[0], ctx->series_len, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    HD_CK(ctx, cudaMemcpyAsync(&ctx->pinned[1], ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HD_CK(ctx, cudaStreamSynchronize(ctx->stream));
-    const hd_status f = check_flags(ctx);
+    const int64_t len = ctx->pinned[0];
+    const hd_status f = flags_status(ctx, int(ctx->pinned[1] & 0xffffffff));
     if (f != HD_OK) return f;
     const int64_t n = std::min(len, max_steps);
     if (out && n > 0)
