@@ -103,7 +103,8 @@ typedef struct hd_opts {
                                 one cell row beyond its own cells and a rebuild
                                 moves a disk by at most one cell).  Same chain.
                                 0: automatic (16 when the colour pass is 1.5 to
-                                3.5 waves of resident blocks deep, else none);
+                                3.5 waves of resident blocks deep, 8 when it is
+                                deeper, none when it is shallower);
                                 1: none; 2 .. 64: K strips (at most m / 2, and
                                 only for one replica, the split kernels and one
                                 thread per cell; else HD_ERR_ARG) [0]          */

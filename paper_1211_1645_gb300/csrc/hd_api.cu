@@ -38,6 +38,7 @@ constexpr int kMaxBins = 512;
 constexpr size_t kCellPad = 64;  // elements of padding after every per-generation cell array
 constexpr int kMaxStrips = 64;    // strips of a one-replica graph wavefront
 constexpr int kAutoStrips = 16;   // strips chosen when the colour pass is 1.5 to 3.5 waves deep
+constexpr int kAutoStripsDeep = 8;  // ... and when it is deeper
 constexpr int kMaxBranches = 64;  // replicas on concurrent branches of a captured step
 
 struct Plan {
@@ -935,10 +936,11 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
     }
     // Concurrent branches of captured steps.  One replica: K strips when
     // asked, or automatically 16 when its colour pass is 1.5 to 3.5 waves of
-    // resident blocks deep (measured on GB300 at N = 2^18 .. 2^22: there the
-    // launch tails are a large share of a pass; shallower passes lose more to
-    // the extra graph nodes than the overlap gains, deeper ones have little
-    // tail to hide).  Several replicas: one branch each, up to kMaxBranches.
+    // resident blocks deep and 8 when it is deeper (measured on GB300 from
+    // N = 2^16 to 2^24: 10-14% faster from N = 2^20 up, where launch tails
+    // and phase boundaries are a large share of a sweep; shallower passes
+    // lose more to the extra graph nodes than the overlap gains).  Several
+    // replicas: one branch each, up to kMaxBranches.
     if (ok && R == 1 && split1) {
         if (o.strips >= 2) {
             ctx->strips = o.strips;
@@ -948,7 +950,8 @@ hd_status hd_batch_init(hd_ctx** out, int32_t R, const int64_t* N, const double*
                  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
                  hd::pass_blocks_per_sm(ctx->cfg(), &per_sm) == cudaSuccess;
             const double waves = (sms > 0 && per_sm > 0) ? double(ctx->blocks_act) / (double(sms) * per_sm) : 0.0;
-            if (ok && waves >= 1.5 && waves < 3.5 && ctx->reps[0].hm >= 2 * kAutoStrips) ctx->strips = kAutoStrips;
+            const int k = waves < 3.5 ? kAutoStrips : kAutoStripsDeep;
+            if (ok && waves >= 1.5 && ctx->reps[0].hm >= 2 * k) ctx->strips = k;
         }
     }
     ctx->branches = R > 1 && R <= kMaxBranches && split1 && o.replica_branches == 0;

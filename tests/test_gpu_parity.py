@@ -598,7 +598,7 @@ def test_strip_wavefront_full_size(hd):
         elif K == 7:
             assert gb == 7
         else:
-            assert gb in (1, 16)  # 16 where the colour pass is 1.5 to 3.5 waves deep
+            assert gb in (1, 16)  # 16 where the colour pass is 1.5 to 3.5 waves deep (1.85 on GB300)
         g.run(2, 50, measure=True)
         runs[K] = (g.positions(), g.stats(), g.series())
         g.close()
@@ -606,6 +606,30 @@ def test_strip_wavefront_full_size(hd):
         assert np.array_equal(runs[K][0], runs[1][0])
         assert np.array_equal(runs[K][1][0], runs[1][1][0]) and np.array_equal(runs[K][1][1], runs[1][1][1])
         assert np.array_equal(runs[K][2], runs[1][2])
+
+
+def test_strip_wavefront_shifted_rows_N4194304(hd):
+    """N = 2048^2 at eta = 0.720 from the shifted-row lattice with the local
+    psi_j field kept per measurement (the fifth configuration's step): the
+    automatic strips (8 where the pass is deeper than 3.5 waves) give the
+    same chain, series and psi_j field as the serial step graph."""
+    import torch
+    N = 2048 * 2048
+    out = {}
+    for K in (1, 0):
+        g = hd.HardDisks(N, 0.720, 0.1, 5, precision="fixed", lattice="triangular", strips=K)
+        gb = g.geometry()["graph_branches"]
+        assert gb == 1 if K == 1 else gb in (1, 8, 16)
+        g.run(2, 25, measure=2)
+        field = torch.empty(2 * N, dtype=torch.float64, device="cuda")
+        g.psi6_local_device(field.data_ptr())
+        torch.cuda.synchronize()
+        out[K] = (g.positions(), g.series(), g.stats(), field.cpu().numpy())
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2][0], out[1][2][0])
+    assert np.array_equal(out[0][3], out[1][3])
 
 
 @pytest.mark.parametrize("form", ["fixed", "fp64"])
