@@ -33,6 +33,24 @@ __device__ __forceinline__ void bin_fp64_dev(double t, const Rep& r, int& c, dou
     u = uu;
 }
 
+// floor(X / W) for 0 <= X < 2^53 and 0 < W < 2^31 with a quotient below 2^31:
+// a float estimate (relative error below 2^-21, so within one of the
+// quotient for quotients below 2^20, and corrected step by step otherwise)
+// made exact with integer arithmetic, instead of a 64-bit integer division.
+__device__ __forceinline__ int64_t floor_div_pos(int64_t X, int32_t W) {
+    int64_t q = int64_t(__fmul_rn(__ll2float_rn(X), __frcp_rn(float(W))));
+    int64_t r = X - q * int64_t(W);
+    while (r < 0) {
+        --q;
+        r += W;
+    }
+    while (r >= int64_t(W)) {
+        ++q;
+        r -= W;
+    }
+    return q;
+}
+
 template <bool FIX, int CAP>
 __global__ void __launch_bounds__(256)
 k_bin(const Rep* __restrict__ reps, int R, int64_t Ntot, double sigma, const double* __restrict__ xy,
@@ -46,7 +64,9 @@ k_bin(const Rep* __restrict__ reps, int R, int64_t Ntot, double sigma, const dou
         if (reps[mid].id_off <= i) lo = mid; else hi = mid - 1;
     }
     const Rep& rep = reps[lo];
-    const double px = __ddiv_rn(xy[2 * i], sigma), py = __ddiv_rn(xy[2 * i + 1], sigma);
+    // a division by 1 is exact: skip it (the FP64 pipe is narrow)
+    const double px = sigma == 1.0 ? xy[2 * i] : __ddiv_rn(xy[2 * i], sigma);
+    const double py = sigma == 1.0 ? xy[2 * i + 1] : __ddiv_rn(xy[2 * i + 1], sigma);
     if (!isfinite(px) || !isfinite(py)) {
         atomicOr(err, kErrBinInput);
         return;
@@ -54,14 +74,21 @@ k_bin(const Rep* __restrict__ reps, int R, int64_t Ntot, double sigma, const dou
     int cx, cy;
     P2<FIX> q;
     if constexpr (FIX) {
-        int64_t X = llround(__dmul_rn(px, 16777216.0)) % rep.LF;
-        int64_t Y = llround(__dmul_rn(py, 16777216.0)) % rep.LF;
-        if (X < 0) X += rep.LF;
-        if (Y < 0) Y += rep.LF;
-        cx = int(X / rep.W);
-        cy = int(Y / rep.W);
-        q.x = int32_t(X % rep.W);
-        q.y = int32_t(Y % rep.W);
+        int64_t X = llround(__dmul_rn(px, 16777216.0));
+        int64_t Y = llround(__dmul_rn(py, 16777216.0));
+        // wrapped into [0, LF); a coordinate already inside needs no division
+        if (X < 0 || X >= rep.LF) {
+            X %= rep.LF;
+            if (X < 0) X += rep.LF;
+        }
+        if (Y < 0 || Y >= rep.LF) {
+            Y %= rep.LF;
+            if (Y < 0) Y += rep.LF;
+        }
+        cx = int(floor_div_pos(X, rep.W));
+        cy = int(floor_div_pos(Y, rep.W));
+        q.x = int32_t(X - int64_t(cx) * rep.W);
+        q.y = int32_t(Y - int64_t(cy) * rep.W);
     } else {
         double x = fmod(px, rep.L), y = fmod(py, rep.L);
         if (x < 0.0) x = __dadd_rn(x, rep.L);

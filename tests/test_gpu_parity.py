@@ -690,3 +690,38 @@ def test_wavefront_across_draw_tables(hd, oracle_mod, form):
         assert np.array_equal(xy[off:off + Ns[r]], o.positions())
         off += Ns[r]
     g.close()
+
+
+@pytest.mark.parametrize("form", ["fixed", "fp64"])
+def test_set_positions_full_size(hd, oracle_mod, form):
+    """hd_set_positions at N = 1024^2 (cell indices up to 1071): the oracle's
+    configuration after two sweeps, a tenth of it moved to periodic images,
+    binned on the device equals the oracle's binning, and the chains
+    continue together."""
+    N = 1024 * 1024
+    g, o = make_pair(hd, oracle_mod, form, N, 0.716, 0.1, 3)
+    g.sweep(2)  # the sweep counters (keys of the draws) stay; only the positions are replaced
+    o.sweep(2)
+    xy = o.positions()
+    rng = np.random.default_rng(4)
+    pick = rng.random(N) < 0.1
+    xy[pick] += rng.integers(-3, 4, size=(int(pick.sum()), 2)) * o.geometry()["L"]
+    g.set_positions(xy)
+    o.set_positions(xy)
+    assert np.array_equal(g.positions(), o.positions())
+    g.sweep(2)
+    o.sweep(2)
+    assert np.array_equal(g.positions(), o.positions())
+
+
+def test_set_positions_with_sigma(hd):
+    """With a disk radius sigma != 1, positions are given in length units and
+    divided by sigma before binning; in the fixed form every position is a
+    multiple of 2^-24 sigma, so handing the positions back is exact."""
+    for sigma in (1.5, 0.25):
+        g = hd.HardDisks(4096, 0.70, 0.1, 9, sigma=sigma, precision="fixed")
+        g.sweep(5)
+        xy = g.positions()
+        g.set_positions(xy)
+        assert np.array_equal(g.positions(), xy)
+        g.close()
