@@ -90,7 +90,9 @@ k_bin(const Rep* __restrict__ reps, int R, int64_t Ntot, double sigma, const dou
         q.x = int32_t(X - int64_t(cx) * rep.W);
         q.y = int32_t(Y - int64_t(cy) * rep.W);
     } else {
-        double x = fmod(px, rep.L), y = fmod(py, rep.L);
+        // fmod returns a coordinate already in [0, L) unchanged
+        double x = (px >= 0.0 && px < rep.L) ? px : fmod(px, rep.L);
+        double y = (py >= 0.0 && py < rep.L) ? py : fmod(py, rep.L);
         if (x < 0.0) x = __dadd_rn(x, rep.L);
         if (y < 0.0) y = __dadd_rn(y, rep.L);
         if (x >= rep.L) x = 0.0;
