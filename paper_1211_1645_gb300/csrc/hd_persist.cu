@@ -99,10 +99,9 @@ k_sweep_persist(const Rep* __restrict__ reps, int R, const Rep rep1, const Frame
                 int* __restrict__ err, uint32_t* sync, uint32_t polls, int stall_band) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) unsigned char s_raw[];
-    int2* s_nbr = reinterpret_cast<int2*>(s_raw);
-    P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + (FIX ? size_t(blockDim.x) * kNbrStride * sizeof(int2) : 0));
+    P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + size_t(blockDim.x) * nbr_bytes_per_thread<FIX>());
     int32_t* s_crowd_id = reinterpret_cast<int32_t*>(s_crowd + size_t(blockDim.x) * CAP);
-    int2* mine = s_nbr + threadIdx.x * kNbrStride;
+    int2* mine = nbr_area<FIX>(s_raw);
     P2<FIX>* sp = s_crowd + threadIdx.x * CAP;
     int32_t* si = s_crowd_id + threadIdx.x * CAP;
     __shared__ uint32_t s_first, s_next;

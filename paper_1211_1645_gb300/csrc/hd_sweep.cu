@@ -135,8 +135,7 @@ k_pass(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const 
        const uint8_t* __restrict__ cnt, P2<FIX>* pos, int32_t* pid, unsigned long long* __restrict__ counters) {
     pdl_begin();
     extern __shared__ __align__(16) unsigned char s_raw[];
-    int2* s_nbr = reinterpret_cast<int2*>(s_raw);
-    P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + (FIX ? size_t(blockDim.x) * kNbrStride * sizeof(int2) : 0));
+    P2<FIX>* s_crowd = reinterpret_cast<P2<FIX>*>(s_raw + size_t(blockDim.x) * nbr_bytes_per_thread<FIX>());
     int32_t* s_crowd_id = reinterpret_cast<int32_t*>(s_crowd + size_t(blockDim.x) * CAP);
     const int r = ONE ? 0 : int(rep_of[blockIdx.x]);
     const Rep rep = ONE ? rep1 : reps[r];
@@ -145,7 +144,7 @@ k_pass(const Rep* __restrict__ reps, const uint16_t* __restrict__ rep_of, const 
     const int col = int(f.perm >> (2 * p)) & 3;
     uint32_t att = 0, acc = 0;
     if (a < a_hi && a < uint32_t(rep.hh)) {
-        pass_cell<FIX, CAP, NTC, false>(rep, f, col, a, cnt, pos, pid, s_nbr + threadIdx.x * kNbrStride,
+        pass_cell<FIX, CAP, NTC, false>(rep, f, col, a, cnt, pos, pid, nbr_area<FIX>(s_raw),
                                         s_crowd + threadIdx.x * CAP, s_crowd_id + threadIdx.x * CAP, att, acc);
     }
     block_count(att, acc, counters, r);

@@ -9,22 +9,40 @@
 
 namespace hd {
 
-// Per-thread shared area of the fixed form: 8 neighbours x kEagerSlots slots,
-// plus one pad entry so that a warp's 8-byte accesses take the minimum two
-// shared-memory wavefronts.
+// Shared staging of the neighbours' slots.  Fixed form: per thread 8
+// neighbours x kEagerSlots slots plus one pad entry (17 int2, thread-major),
+// so that a warp's 8-byte accesses take the minimum two shared-memory
+// wavefronts.  FP64 form: slot 0 of the 8 neighbours (16 bytes each), stored
+// slot-major (entry q of thread t at q * blockDim + t), so that consecutive
+// threads' 16-byte entries are consecutive and need no pad.
 constexpr int kNbrStride = 17;
+
+template <bool FIX>
+__host__ __device__ constexpr size_t nbr_bytes_per_thread() {
+    return FIX ? size_t(kNbrStride) * sizeof(int2) : size_t(8) * sizeof(double2);
+}
+
+// This thread's staging pointer (FP64: its entry of slot-major row 0).
+template <bool FIX>
+__device__ __forceinline__ int2* nbr_area(unsigned char* s_raw) {
+    if constexpr (FIX) return reinterpret_cast<int2*>(s_raw) + size_t(threadIdx.x) * kNbrStride;
+    else return reinterpret_cast<int2*>(reinterpret_cast<double2*>(s_raw) + threadIdx.x);
+}
 
 // ... followed by each thread's area for the occupants of a crowded cell
 // (more than kEagerSlots disks): CAP positions and CAP ids.
 template <bool FIX, int CAP>
 constexpr size_t pass_smem(int threads) {
-    return (FIX ? size_t(threads) * kNbrStride * sizeof(int2) : 0) + size_t(threads) * CAP * (sizeof(P2<FIX>) + 4);
+    return size_t(threads) * nbr_bytes_per_thread<FIX>() + size_t(threads) * CAP * (sizeof(P2<FIX>) + 4);
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
 
 
 // Rebuild by scatter of two old cells of one replica (replica-local planar
@@ -189,6 +207,19 @@ __device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int co
             cp_async8(sm + uint32_t(2 * q) * 8u, pos + ci);
             cp_async8(sm + uint32_t(2 * q + 1) * 8u, pos + rep.stride32 + ci);
         }
+    } else {
+        // FP64: the occupancies and slot 0 of every neighbour, staged before
+        // the cell's own loads and draws (slots beyond 0 of the neighbours
+        // that hold more disks are loaded in the test)
+        const uint32_t sm = static_cast<uint32_t>(__cvta_generic_to_shared(mine));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (i == 4) continue;
+            const int q = i < 4 ? i : i - 1;
+            const uint32_t ci = yp[i / 3] + xp[i % 3];
+            nocc |= uint32_t(occupancy<CAP, COH>(cnt, ci)) << (4 * q);
+            cp_async16(sm + uint32_t(q) * blockDim.x * 16u, pos + ci);
+        }
     }
     CellRegs<FIX, true> own;
     load_cell<FIX, true, CAP, COH>(cnt, pos, pid, rep.stride32, cell, own);
@@ -224,14 +255,29 @@ __device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int co
                         ok &= pair_clear<FIX>(ld_cell<COH>(pos + size_t(k) * rep.stride32 + ci), ox, oy, np, rep);
                 }
             } else {
+                cp_async_wait_all();  // a no-op after the first trial
+                const double2* nb = reinterpret_cast<const double2*>(mine);
+                // FP64 arithmetic bounds the FP64 form: a pair is tested only
+                // while the move still stands
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    if (i == 4 || !ok) continue;
+                    if (i == 4) continue;
+                    const int q = i < 4 ? i : i - 1;
                     const int ox = i % 3 - 1, oy = i / 3 - 1;
-                    CellRegs<FIX, false> c;
-                    load_cell<FIX, false, CAP, COH>(cnt, pos, nullptr, rep.stride32, yp[i / 3] + xp[i % 3], c);
-                    for (int k = 0; k < c.n && ok; ++k)
-                        ok = pair_clear<FIX>(c.template slot<COH>(k, pos, rep.stride32), ox, oy, np, rep);
+                    const int ni = int(nocc >> (4 * q)) & 0xF;
+                    if (ok && ni >= 1) ok = pair_clear<FIX>(nb[size_t(q) * blockDim.x], ox, oy, np, rep);
+                }
+                // neighbours of two or more disks (a nibble n >= 2 is the one
+                // whose n + 6 sets its bit 3): their further slots from memory
+                for (uint32_t cm = (nocc + 0x66666666u) & 0x88888888u; cm != 0u && ok; cm &= cm - 1u) {
+                    const int q = (__ffs(int(cm)) - 1) >> 2;
+                    const int i = q + (q >= 4 ? 1 : 0);
+                    const int ox = int((0x24924u >> (2 * i)) & 3u) - 1;  // i % 3 - 1
+                    const int oy = int((0x2A540u >> (2 * i)) & 3u) - 1;  // i / 3 - 1
+                    const int ni = int(nocc >> (4 * q)) & 0xF;
+                    const uint32_t ci = rep.coff + row_part(rep, wrap_cell(cy + oy, m)) + col_part(rep, wrap_cell(cx + ox, m));
+                    for (int k = 1; k < ni && ok; ++k)
+                        ok = pair_clear<FIX>(ld_cell<COH>(pos + size_t(k) * rep.stride32 + ci), ox, oy, np, rep);
                 }
             }
             return ok;
@@ -278,7 +324,7 @@ __device__ __forceinline__ void pass_cell(const Rep& rep, const Frame& f, int co
         att += uint32_t(rep.nt);
     }
     // no copy may still be landing in shared memory when the thread moves on
-    if constexpr (FIX) cp_async_wait_all();
+    cp_async_wait_all();
 }
 
 }  // namespace hd
