@@ -53,8 +53,10 @@ typedef enum hd_lattice {
     HD_LATTICE_TRIANGULAR = 1 /* same, odd rows shifted by half a spacing        */
 } hd_lattice;
 
-/* Options shared by all replicas of a context.  Zero / negative fields take
- * the default given in brackets. */
+/* Options shared by all replicas of a context.  A zero field takes the
+ * default given in brackets; so does a negative hist_bins, hist_dr, cell_min,
+ * block_threads or threads_per_cell, while any other negative field is
+ * HD_ERR_ARG. */
 typedef struct hd_opts {
     int32_t precision;       /* hd_precision [HD_FP64]                              */
     int32_t lattice;         /* hd_lattice [HD_LATTICE_SQUARE]                      */
