@@ -505,26 +505,87 @@ cudaError_t join_side(hd_ctx* ctx, cudaStream_t s, int n) {
     return e;
 }
 
+// One replica's nc sweeps as K strips (see enqueue_strips) on side streams
+// off .. off + K - 1, forked and joined by the caller; c0 is the replica's
+// one-replica launch configuration, tab and counters its draw table and trial
+// counters.  The phase events of side stream x are side_ev[ev_phase + x] and
+// side_ev[ev_phase + S + x] (by phase parity), S the side streams in use.
+cudaError_t enqueue_strip_chain(hd_ctx* ctx, const hd::LaunchCfg& c0, const Rep& rep, const hd::Frame* tab,
+                                unsigned long long* counters, int nc, int cur0, int off, int K, size_t ev_phase,
+                                int S) {
+    std::vector<uint32_t> b(size_t(K) + 1);
+    for (int i = 0; i <= K; ++i) b[size_t(i)] = uint32_t((int64_t(rep.hm) * i) / K);
+    cudaError_t e = cudaSuccess;
+    int cur = cur0;
+    int k = 0;  // phase index over the chunk
+    for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
+        for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph, ++k) {
+            const size_t now = ev_phase + size_t(k & 1) * size_t(S) + size_t(off);
+            const size_t prev = ev_phase + size_t((k & 1) ^ 1) * size_t(S) + size_t(off);
+            for (int i = 0; i < K && e == cudaSuccess; ++i) {
+                cudaStream_t bs = ctx->side[size_t(off + i)];
+                if (k > 0) {  // the previous phase in the two neighbouring strips (its own: stream order)
+                    const int l = (i + K - 1) % K, r = (i + 1) % K;
+                    if (l != i) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(l)], 0);
+                    if (e == cudaSuccess && r != i && r != l) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(r)], 0);
+                    if (e != cudaSuccess) break;
+                }
+                hd::LaunchCfg c = c0;
+                c.stream = bs;
+                const uint32_t lo = b[size_t(i)] * uint32_t(rep.hm), hi = b[size_t(i) + 1] * uint32_t(rep.hm);
+                if (ph == 0) {
+                    c.band_lo = lo;
+                    c.band_span = hi - lo;
+                    e = launch(ctx, HD_K_REBUILD, [&] {
+                        return hd::launch_rebuild(c, tab, j, ctx->buf[cur], ctx->buf[cur ^ 1], ctx->err);
+                    }, true);
+                } else {
+                    c.act_lo = lo;
+                    c.act_hi = hi;
+                    e = launch(ctx, HD_K_PASS, [&] {
+                        return hd::launch_pass(c, tab, j, ph - 1, ctx->buf[cur], counters);
+                    }, true);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(ctx->side_ev[now + size_t(i)], bs);
+            }
+            if (ph == 0) cur ^= 1;
+        }
+    }
+    return e;
+}
+
+// The one-replica launch configuration of replica r of a batch (its blocks
+// numbered from 0, its constants as kernel parameters); rep receives the
+// replica's constants and must outlive the launches.
+hd::LaunchCfg replica_cfg(hd_ctx* ctx, int r, Rep& rep) {
+    rep = ctx->reps[size_t(r)];
+    rep.blk_act = 0;
+    rep.blk_cell = 0;
+    hd::LaunchCfg c = ctx->cfg();
+    c.R = 1;
+    c.rep0 = &rep;
+    c.reps = ctx->reps_d + r;
+    c.ntc = (rep.nt == 1 || rep.nt == 2) ? rep.nt : 0;
+    c.blocks_act = int((int64_t(rep.hh) + c.threads - 1) / c.threads);
+    c.blocks_cell = int((int64_t(rep.m) * rep.m + c.threads - 1) / c.threads);
+    return c;
+}
+
 // Replica branches: the nc sweeps of one draw table, each replica on its own
 // stream with its own one-replica launches (constants as kernel parameters),
 // the replicas' chains running concurrently.  Same chain as the batched
 // launches: the replicas are independent.
+// (Strips inside the branches measured slower: the replicas' concurrency
+// already fills the GPU, and the extra graph nodes only cost launches.)
 cudaError_t enqueue_replica_branches(hd_ctx* ctx, cudaStream_t s, int nc) {
     cudaError_t e = fork_side(ctx, s, ctx->R);
     const int cur0 = ctx->cur;
     for (int r = 0; r < ctx->R && e == cudaSuccess; ++r) {
-        Rep rep = ctx->reps[size_t(r)];  // this replica alone: its blocks start at 0
-        rep.blk_act = 0;
-        rep.blk_cell = 0;
-        hd::LaunchCfg c = ctx->cfg(ctx->side[size_t(r)]);
-        c.R = 1;
-        c.rep0 = &rep;
-        c.reps = ctx->reps_d + r;
-        c.ntc = (rep.nt == 1 || rep.nt == 2) ? rep.nt : 0;
-        c.blocks_act = int((int64_t(rep.hh) + c.threads - 1) / c.threads);
-        c.blocks_cell = int((int64_t(rep.m) * rep.m + c.threads - 1) / c.threads);
+        Rep rep;
+        hd::LaunchCfg c = replica_cfg(ctx, r, rep);
         const hd::Frame* tab = ctx->table + size_t(r) * (hd::kMaxChunk + 1);
         unsigned long long* counters = ctx->counters + 2 * size_t(r);
+        c.stream = ctx->side[size_t(r)];
         int cur = cur0;
         for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
             e = launch(ctx, HD_K_REBUILD, [&] {
@@ -551,46 +612,12 @@ cudaError_t enqueue_replica_branches(hd_ctx* ctx, cudaStream_t s, int nc) {
 // same sequence of phases as in the serial order, so the chain is the same.
 cudaError_t enqueue_strips(hd_ctx* ctx, cudaStream_t s, int nc) {
     const int K = ctx->strips;
-    const Rep& rep = ctx->reps[0];
-    std::vector<uint32_t> b(size_t(K) + 1);
-    for (int i = 0; i <= K; ++i) b[size_t(i)] = uint32_t((int64_t(rep.hm) * i) / K);
     cudaError_t e = fork_side(ctx, s, K);
-    const size_t ev_phase = size_t(1 + K);
-    int cur = ctx->cur;
-    int k = 0;  // phase index over the chunk
-    for (int j = 1; j <= nc && e == cudaSuccess; ++j) {
-        for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph, ++k) {
-            const size_t now = ev_phase + size_t(k & 1) * size_t(K), prev = ev_phase + size_t((k & 1) ^ 1) * size_t(K);
-            for (int i = 0; i < K && e == cudaSuccess; ++i) {
-                cudaStream_t bs = ctx->side[size_t(i)];
-                if (k > 0) {  // the previous phase in the two neighbouring strips (its own: stream order)
-                    const int l = (i + K - 1) % K, r = (i + 1) % K;
-                    if (l != i) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(l)], 0);
-                    if (e == cudaSuccess && r != i && r != l) e = cudaStreamWaitEvent(bs, ctx->side_ev[prev + size_t(r)], 0);
-                    if (e != cudaSuccess) break;
-                }
-                hd::LaunchCfg c = ctx->cfg(bs);
-                const uint32_t lo = b[size_t(i)] * uint32_t(rep.hm), hi = b[size_t(i) + 1] * uint32_t(rep.hm);
-                if (ph == 0) {
-                    c.band_lo = lo;
-                    c.band_span = hi - lo;
-                    e = launch(ctx, HD_K_REBUILD, [&] {
-                        return hd::launch_rebuild(c, ctx->table, j, ctx->buf[cur], ctx->buf[cur ^ 1], ctx->err);
-                    }, true);
-                } else {
-                    c.act_lo = lo;
-                    c.act_hi = hi;
-                    e = launch(ctx, HD_K_PASS, [&] {
-                        return hd::launch_pass(c, ctx->table, j, ph - 1, ctx->buf[cur], ctx->counters);
-                    }, true);
-                }
-                if (e == cudaSuccess) e = cudaEventRecord(ctx->side_ev[now + size_t(i)], bs);
-            }
-            if (ph == 0) cur ^= 1;
-        }
-    }
+    if (e == cudaSuccess)
+        e = enqueue_strip_chain(ctx, ctx->cfg(), ctx->reps[0], ctx->table, ctx->counters, nc, ctx->cur, 0, K,
+                                size_t(1 + K), K);
     if (e == cudaSuccess) e = join_side(ctx, s, K);
-    ctx->cur = cur;
+    if (nc & 1) ctx->cur ^= 1;
     return e;
 }
 
