@@ -725,3 +725,28 @@ def test_set_positions_with_sigma(hd):
         g.set_positions(xy)
         assert np.array_equal(g.positions(), xy)
         g.close()
+
+
+def test_profiled_steps_of_wavefront_contexts(hd):
+    """While profiling, hd_run captures its steps in serial order with a timing
+    event around every kernel, also for a context with strips or replica
+    branches: the chains stay those of the unprofiled graphs and every
+    kernel class of the step is timed."""
+    for kw in ({"N": 4096, "eta": 0.70, "delta": 0.1, "seed": 91, "strips": 3},
+               {"N": [400, 576], "eta": [0.70, 0.71], "delta": [0.1, 0.1], "seed": [92, 93]}):
+        strips = kw.pop("strips", 0)
+        a = hd.HardDisks(kw["N"], kw["eta"], kw["delta"], kw["seed"], precision="fixed", strips=strips)
+        b = hd.HardDisks(kw["N"], kw["eta"], kw["delta"], kw["seed"], precision="fixed", strips=strips)
+        assert a.geometry()["graph_branches"] > 1
+        a.profile(True)
+        a.run(2, 7, measure=True)
+        kt = a.kernel_times()
+        a.profile(False)
+        b.run(2, 7, measure=True)
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.series(), b.series())
+        for cls in ("rebuild", "pass", "hist", "psi6"):
+            assert kt[cls][0] > 0.0 and kt[cls][1] > 0
+        assert kt["pass"][1] == 2 * 7 * 4  # whole passes: the profiled graph has no strips
+        a.close()
+        b.close()
